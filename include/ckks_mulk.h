@@ -1,0 +1,227 @@
+/*
+ * ckks_mulk.h -- C ABI of the GB300 RNS-CKKS multi-input ciphertext
+ * multiplication library (libckks_mulk.so).
+ *
+ * Method: "Multi-Input Ciphertext Multiplication for Homomorphic Encryption"
+ * (Akherati and Zhang). The library multiplies k ciphertexts with the
+ * paper's k-input multiplier: tensor products of child tuples (Eq. 13),
+ * multi-level rescaling at inner nodes (Algorithm 1, Eq. 16-17),
+ * relinearisation of d_2..d_n with the extra evaluation keys ek_t
+ * (Eq. 14-15) summed before a single ModDown per output polynomial
+ * (Section III), the merged INTT and scaled BConv of ModDown (Eq. 11-12),
+ * and the relocated rescale at the root (coefficient-domain rs, Eq. 6,
+ * followed by one NTT; Section IV).
+ *
+ * Conventions (all entry points)
+ *  - Moduli: q_0..q_{L-1} (Q) and p_0..p_{K-1} (P), every prime < 2^61 and
+ *    = 1 mod 2N. "Prime index" x < L means q_x, x >= L means p_{x-L}.
+ *  - A polynomial limb is N uint64 residues in [0, q). The NTT domain is the
+ *    negacyclic evaluation map A[i] = sum_j a_j psi^((2 brv(i) + 1) j) mod q,
+ *    psi = the smallest primitive 2N-th root of unity mod q, brv the
+ *    log2(N)-bit reversal.
+ *  - A tuple (ckks_tuple) is n_polys polynomials of `level` limbs each,
+ *    limb-major: limb j of polynomial a starts at
+ *    data + (a * poly_stride + j) * N. A ciphertext has n_polys = 2.
+ *  - Device pointers are caller-owned device memory on the context's device;
+ *    the library never frees them. Calls are asynchronous and ordered on the
+ *    given CUDA stream (a cudaStream_t passed as void*; NULL = default
+ *    stream). Inputs must stay valid until the stream reaches the call.
+ *  - Evaluation keys for t = 2..t_max, digit beta < dnum:
+ *    keys[t-2][beta][l][x][N] (l = 0, 1; x = prime index, Q rows first),
+ *    NTT domain, with ek_{t,beta} = (-a s + e + [x < L] P G_beta s^t, a),
+ *    G_beta = Qhat_beta [Qhat_beta^-1]_{Q_beta}, Qhat_beta = Q / Q_beta,
+ *    digit beta = primes q_{beta alpha} .. q_{(beta+1) alpha - 1},
+ *    alpha = ceil(L / dnum). For dnum = 1 this is Eq. 2, 9 and 14.
+ *  - Errors: every entry point returns 0 (CKKS_OK) or a negative code;
+ *    nothing throws across the ABI. A CUDA launch error is returned as
+ *    CKKS_ECUDA and also kept as a sticky status (ckks_check).
+ *  - Workspace: the caller allocates it (ckks_workspace_size); the library
+ *    allocates no device memory after context creation.
+ */
+#ifndef CKKS_MULK_H
+#define CKKS_MULK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CKKS_OK 0
+#define CKKS_EINVAL (-1)   /* bad argument: shape, level, flag, partition */
+#define CKKS_ELEVEL (-2)   /* level too low for the partition depth, or > L */
+#define CKKS_EKEY (-3)     /* evaluation-key set lacks ek_t for a needed t */
+#define CKKS_ENOMEM (-4)   /* workspace smaller than ckks_workspace_size */
+#define CKKS_ECUDA (-5)    /* CUDA error (launch or sticky) */
+#define CKKS_ETIMEOUT (-6) /* a bounded device wait ran out */
+#define CKKS_EBUSY (-7)    /* admission refused */
+
+typedef struct ckks_context ckks_context;
+typedef struct ckks_evk_set ckks_evk_set;
+typedef struct ckks_plan ckks_plan;
+
+typedef struct {
+    uint32_t log_n;     /* N = 2^log_n, 4 <= log_n <= 16 */
+    uint32_t L;         /* number of Q primes, 1 <= L, L + K <= 64 */
+    uint32_t K;         /* number of P primes */
+    uint32_t dnum;      /* key-switching digits, 1 <= dnum <= L */
+    const uint64_t *q;  /* host array [L] */
+    const uint64_t *p;  /* host array [K] */
+} ckks_params;
+
+typedef struct {
+    uint64_t *data;       /* device, see "tuple" above */
+    uint32_t n_polys;     /* 2 for a ciphertext, n + 1 for a product of n */
+    uint32_t level;       /* active limbs q_0..q_{level-1} */
+    uint32_t poly_stride; /* limbs between polynomials, >= level */
+    uint32_t ntt_form;    /* 1 = NTT domain (required by ckks_mul_k) */
+    double scale;         /* tracked on the host; not used by the kernels */
+} ckks_tuple;
+
+typedef struct {
+    uint64_t limb_ntt;     /* limb forward transforms enqueued */
+    uint64_t limb_intt;    /* limb inverse transforms enqueued */
+    uint64_t ntt_phase;    /* forward transform kernel launches */
+    uint64_t intt_phase;   /* inverse transform kernel launches */
+    uint64_t bconv;        /* basis conversions (ModUp digits and ModDowns) */
+    uint64_t kernels;      /* every kernel launch */
+} ckks_op_counters;
+
+/* ---------------------------------------------------------------- context
+ * ckks_context_create: validates the parameters (primes < 2^61, prime,
+ * = 1 mod 2N, pairwise distinct) and builds the twiddle, BConv, rescale
+ * (Eq. 16) and key-preparation tables on `device`. The context owns these
+ * tables (one device allocation) until ckks_context_destroy.
+ * Returns CKKS_EINVAL for bad parameters, CKKS_ECUDA if the device
+ * allocation fails. */
+int ckks_context_create(const ckks_params *params, int device, ckks_context **out);
+void ckks_context_destroy(ckks_context *ctx);
+
+/* ---------------------------------------------------------------- keys
+ * ckks_keygen_evk: evaluation keys for t = 2..t_max from the secret s
+ * (device int64 [N], coefficients in {-1, 0, 1}), the masks a (device
+ * [t_max-1][dnum][L+K][N] residues, NTT domain) and the errors e (device
+ * int64 [t_max-1][dnum][N]); writes keys [t_max-1][dnum][2][L+K][N] in the
+ * layout of the conventions (Eq. 2, 9, 14 with the digit gadget).
+ * Workspace: ckks_keygen_workspace_size bytes. */
+int ckks_keygen_workspace_size(const ckks_context *ctx, size_t *bytes);
+int ckks_keygen_evk(ckks_context *ctx, uint32_t t_max, const int64_t *s, const uint64_t *a, const int64_t *e,
+                    uint64_t *keys, void *workspace, size_t ws_bytes, void *stream);
+
+/* ckks_evk_set_create: adopts a key buffer in the layout above for
+ * t = 2..t_max. The buffer is converted IN PLACE to the library's internal
+ * form (Montgomery form; P^-1 folded into the Q rows, Eq. 12) and is
+ * borrowed until ckks_evk_set_destroy; do not read it as plain keys after. */
+int ckks_evk_set_create(ckks_context *ctx, uint32_t t_max, uint64_t *keys, void *stream, ckks_evk_set **out);
+void ckks_evk_set_destroy(ckks_evk_set *set);
+
+/* ---------------------------------------------------------------- plans
+ * ckks_plan_create: the partition tree of a k-input multiply (2 <= k <= 12)
+ * in the notation of Table II, e.g. "(4,3)|(2,2)": '|' separates layers and
+ * each group list of a layer splits, left to right, the next group of the
+ * layer above with the same size. NULL selects Table II's optimised
+ * partition. CKKS_EINVAL if the text does not parse or breaks the depth rule
+ * (Section V-C: rescales on any path <= ceil(log2 k)). */
+int ckks_plan_create(ckks_context *ctx, uint32_t k, const char *partition, ckks_plan **out);
+void ckks_plan_destroy(ckks_plan *plan);
+/* depth = rescales on the longest path (output level = input level - depth);
+ * rs_units = Table II's rescale-unit count below the root. */
+int ckks_plan_describe(const ckks_plan *plan, uint32_t *depth, uint32_t *rs_units, uint32_t *n_nodes);
+
+/* Workspace bytes for ckks_mul_k / ckks_mul_k_batch at this input level and
+ * batch size. CKKS_ELEVEL if level <= depth or level > L. */
+int ckks_workspace_size(const ckks_context *ctx, const ckks_plan *plan, uint32_t level, uint32_t batch,
+                        size_t *bytes);
+
+/* ---------------------------------------------------------------- multiply
+ * ckks_mul_k: out = product of the k ciphertexts ct[0..k-1] (all NTT domain,
+ * same level) with the plan's tree. out->data must hold 2 polynomials of
+ * level - depth limbs (poly_stride >= that); out is written in the NTT
+ * domain and out->level / out->scale are set (scale = product of input
+ * scales / product of the divided primes). The result equals, residue for
+ * residue, the oracle's evaluation: inner nodes rescaled mu = m-1 times,
+ * root relinearised with ek_2..ek_n then rescaled m-1 times.
+ * CKKS_EKEY if the set's t_max < k. */
+int ckks_mul_k(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, const ckks_evk_set *evk,
+               const ckks_plan *plan, ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream);
+
+/* ckks_mul_k_batch: `batch` independent products with one plan and one key
+ * set, each kernel launch covering the whole batch. ct is [batch][k] tuples,
+ * out is [batch]. For every input position u, ct[b*k+u].data must be
+ * ct[u].data + b * stride_u for one stride_u (likewise for out); the same
+ * level, poly_stride and n_polys for all b. */
+int ckks_mul_k_batch(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uint32_t batch, const ckks_evk_set *evk,
+                     const ckks_plan *plan, ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream);
+
+/* ckks_mul2: the standard 2-input multiply of Section II (Eq. 1-7): tensor
+ * product, relinearisation with ModDown finished in the NTT domain, one RS in
+ * the NTT domain (Eq. 7). The comparator for chained multiplication. Output
+ * level = min input level - 1. Workspace: ckks_mul2_workspace_size.
+ * ckks_mul2_batch: `batch` such products; a, b and out are [batch] arrays
+ * with a constant pointer stride each (as in ckks_mul_k_batch). */
+int ckks_mul2_workspace_size(const ckks_context *ctx, uint32_t level, uint32_t batch, size_t *bytes);
+int ckks_mul2(ckks_context *ctx, const ckks_tuple *a, const ckks_tuple *b, const ckks_evk_set *evk,
+              ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream);
+int ckks_mul2_batch(ckks_context *ctx, const ckks_tuple *a, const ckks_tuple *b, uint32_t batch,
+                    const ckks_evk_set *evk, ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- steps
+ * ckks_tensor (Eq. 13): out = product of m tuples (NTT domain, coefficient-
+ * wise in each limb), out->n_polys = sum(n_polys) - m + 1, level = min
+ * input level (higher inputs drop their top limbs). */
+int ckks_tensor(ckks_context *ctx, const ckks_tuple *in, uint32_t m, ckks_tuple *out, void *stream);
+
+/* ckks_relin (Eq. 15 with the combined ModDown): d has n + 1 polynomials
+ * (NTT domain, n >= 2, ek_t for t <= n needed); out (2 polynomials, same
+ * level) gets (d_0, d_1) + sum_t ceil(P^-1 d_t ek_t), in the coefficient
+ * domain if out_ntt = 0 (Eq. 11 merged form), else NTT domain.
+ * Workspace: ckks_relin_workspace_size. */
+int ckks_relin_workspace_size(const ckks_context *ctx, uint32_t n, uint32_t level, size_t *bytes);
+int ckks_relin(ckks_context *ctx, const ckks_tuple *d, const ckks_evk_set *evk, uint32_t out_ntt, ckks_tuple *out,
+               void *workspace, size_t ws_bytes, void *stream);
+
+/* ckks_rescale_multi (Algorithm 1): mu combined rescales of every polynomial
+ * of `in` (NTT domain) -> out (level - mu, NTT domain); mu = 1 is Eq. 7.
+ * in and out may be the same tuple. Workspace:
+ * ckks_rescale_workspace_size. */
+int ckks_rescale_workspace_size(const ckks_context *ctx, uint32_t n_polys, uint32_t level, uint32_t mu,
+                                size_t *bytes);
+int ckks_rescale_multi(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckks_tuple *out, void *workspace,
+                       size_t ws_bytes, void *stream);
+
+/* Forward / inverse transform of every limb of a tuple (in and out may be
+ * the same tuple); sets out->ntt_form. */
+int ckks_ntt(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *stream);
+int ckks_intt(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *stream);
+
+/* ---------------------------------------------------------------- status
+ * ckks_counters: operation counts enqueued since the last reset (reset != 0
+ * clears them after reading). Counts are taken on the host when work is
+ * enqueued, so they need no GPU to read. */
+int ckks_counters(ckks_context *ctx, ckks_op_counters *out, int reset);
+/* Kernel timing hook (tracing). ckks_profile_enable(ctx, 1) clears earlier
+ * records and, until ckks_profile_enable(ctx, 0), records a CUDA event pair
+ * on the launch stream around every kernel the library enqueues (events
+ * are created by the library on first use, never device memory).
+ * ckks_profile_read waits for the recorded events and returns, per kernel
+ * class, the launch count, the summed event time and the summed algorithmic
+ * bytes (each input and output limb of a launch counted once). */
+typedef struct {
+    char name[24];
+    uint64_t launches;
+    double total_ms;
+    double alg_bytes;
+} ckks_kernel_stats;
+int ckks_profile_enable(ckks_context *ctx, int enable);
+int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, uint32_t *n_out);
+
+/* ckks_check: CKKS_ECUDA if a CUDA error is pending on the context's device
+ * (sticky launch error or cudaGetLastError), else CKKS_OK. */
+int ckks_check(ckks_context *ctx);
+const char *ckks_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CKKS_MULK_H */

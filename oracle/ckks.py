@@ -183,13 +183,10 @@ def bconv(y: np.ndarray, src: list[int], dst: list[int]) -> np.ndarray:
     qhat_j = (prod src) / q_j, for each destination modulus x. Computed with
     residues; `bconv_bigint` is the same integer S written with big ints."""
     Qs = prod(src)
-    ys = [ring.smul(y[j], ring.inv(Qs // qj, qj), qj) for j, qj in enumerate(src)]
+    ys = np.stack([ring.smul(y[j], ring.inv(Qs // qj, qj), qj) for j, qj in enumerate(src)])
     out = np.empty((len(dst), y.shape[1]), dtype=np.uint64)
     for i, x in enumerate(dst):
-        acc = np.zeros(y.shape[1], dtype=np.uint64)
-        for j, qj in enumerate(src):
-            acc = ring.addmod(acc, ring.smul(ys[j] % np.uint64(x), (Qs // qj) % x, x), x)
-        out[i] = acc
+        out[i] = ring.dot_const(ys, [(Qs // qj) % x for qj in src], x)
     return out
 
 
@@ -248,16 +245,23 @@ def key_rows(ctx: Ctx, level: int) -> list[int]:
 # ---------------------------------------------------------------------------
 # Eq. 2 / 9 / 14: evaluation keys
 # ---------------------------------------------------------------------------
-def keygen(ctx: Ctx, s: np.ndarray, a: np.ndarray, e: np.ndarray, t: int, beta: int):
+def secret_ntt(ctx: Ctx, s: np.ndarray) -> np.ndarray:
+    primes = ctx.q + ctx.p
+    return ntt_poly(np.stack([ring.from_signed(s, x) for x in primes]), primes)
+
+
+def keygen(ctx: Ctx, s: np.ndarray, a: np.ndarray, e: np.ndarray, t: int, beta: int, S=None, St=None):
     """ek_{t,beta} = (-a s + e + [Q limb] P G_beta s^t, a), NTT domain, all
     L + K limbs. s and e are small signed coefficient vectors; a is given in
-    the NTT domain."""
+    the NTT domain. S = NTT(s) and St = NTT(s)^t may be passed in."""
     primes = ctx.q + ctx.p
-    S = ntt_poly(np.stack([ring.from_signed(s, x) for x in primes]), primes)
+    if S is None:
+        S = secret_ntt(ctx, s)
     E = ntt_poly(np.stack([ring.from_signed(e, x) for x in primes]), primes)
-    St = S.copy()
-    for _ in range(t - 1):
-        St = ring.mulmod_rows(St, S, primes)
+    if St is None:
+        St = S.copy()
+        for _ in range(t - 1):
+            St = ring.mulmod_rows(St, S, primes)
     G = ctx.gadget(beta)
     ek0 = np.empty_like(a)
     for x, m in enumerate(primes):
@@ -270,8 +274,14 @@ def keygen(ctx: Ctx, s: np.ndarray, a: np.ndarray, e: np.ndarray, t: int, beta: 
 
 def keygen_all(ctx: Ctx, km, t_max: int):
     """keys[t-2][beta] = (ek0, ek1) for t = 2..t_max from synth.KeyMaterial."""
-    return [[keygen(ctx, km.s, km.a[t - 2][b], km.e[t - 2][b], t, b) for b in range(ctx.dnum)]
-            for t in range(2, t_max + 1)]
+    primes = ctx.q + ctx.p
+    S = secret_ntt(ctx, km.s)
+    St = S.copy()
+    out = []
+    for t in range(2, t_max + 1):
+        St = ring.mulmod_rows(St, S, primes)
+        out.append([keygen(ctx, km.s, km.a[t - 2][b], km.e[t - 2][b], t, b, S, St) for b in range(ctx.dnum)])
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -117,6 +117,16 @@ def smul(a, c: int, q: int) -> np.ndarray:
     return out
 
 
+def dot_const(rows: np.ndarray, consts, q: int) -> np.ndarray:
+    """sum_j rows[j] * consts[j] mod q (rows [m][n], any uint64 entries)."""
+    rows = _u64(rows)
+    c = _u64([int(x) % q for x in consts])
+    m, n = rows.shape
+    out = np.empty(n, dtype=np.uint64)
+    _lib().or_dot_const(_p(rows), _p(c), m, _p(out), n, q)
+    return out
+
+
 def addmod(a, b, q: int) -> np.ndarray:
     return (_u64(a) % np.uint64(q) + _u64(b) % np.uint64(q)) % np.uint64(q)
 

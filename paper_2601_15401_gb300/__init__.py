@@ -1,0 +1,293 @@
+"""Python binding of libckks_mulk.so (include/ckks_mulk.h): argument
+marshalling only. Every step of the multiplication runs in the library's CUDA
+kernels; there is no CPU or PyTorch fallback: the first call into the library
+(e.g. creating a Context) raises ImportError when libckks_mulk.so is missing.
+
+Device memory and streams come from PyTorch: tuples are torch.uint64 CUDA
+tensors shaped [n_polys][poly_stride][N] (or [batch][n_polys][stride][N]).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from ._lib import ERRORS, CkksError, lib, library_path
+
+__all__ = ["Context", "Tuple", "CkksError", "library_path", "lib", "TABLE_II"]
+
+TABLE_II = {
+    2: "(1,1)", 3: "(1,1,1)", 4: "(2,2)", 5: "(2,2,1)", 6: "(3,3)", 7: "(4,3)|(2,2)",
+    8: "(4,4)|(2,2),(2,2)", 9: "(3,3,3)", 10: "(3,3,4)|(2,2)", 11: "(4,4,3)|(2,2),(2,2)",
+    12: "(6,6)|(3,3),(3,3)",
+}
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("L", ctypes.c_uint32), ("K", ctypes.c_uint32),
+                ("dnum", ctypes.c_uint32), ("q", ctypes.POINTER(ctypes.c_uint64)),
+                ("p", ctypes.POINTER(ctypes.c_uint64))]
+
+
+class _Tuple(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n_polys", ctypes.c_uint32), ("level", ctypes.c_uint32),
+                ("poly_stride", ctypes.c_uint32), ("ntt_form", ctypes.c_uint32), ("scale", ctypes.c_double)]
+
+
+class _KStats(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("alg_bytes", ctypes.c_double)]
+
+
+class _Counters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("limb_ntt", "limb_intt", "ntt_phase", "intt_phase", "bconv", "kernels")]
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise CkksError(rc, f"{what}: {ERRORS.get(rc, rc)} ({lib().ckks_strerror(rc).decode()})")
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+@dataclass
+class Tuple:
+    """A tuple of polynomials in device memory.
+
+    data: torch.uint64 CUDA tensor; polynomial a, limb j lives at
+    data.view(-1)[(a * poly_stride + j) * N : ...]."""
+    data: object
+    n_polys: int
+    level: int
+    poly_stride: int
+    ntt_form: int = 1
+    scale: float = 1.0
+
+    def c(self) -> _Tuple:
+        return _Tuple(self.data.data_ptr(), self.n_polys, self.level, self.poly_stride, self.ntt_form, self.scale)
+
+    @staticmethod
+    def wrap(t, level=None, ntt_form=1, scale=1.0) -> "Tuple":
+        """t: [n_polys][stride][N] tensor."""
+        n_polys, stride = int(t.shape[0]), int(t.shape[1])
+        return Tuple(t, n_polys, level if level is not None else stride, stride, ntt_form, scale)
+
+    def limbs(self):
+        """View [n_polys][level][N] of the active limbs."""
+        return self.data[:, :self.level]
+
+
+class Context:
+    """One parameter set (N, Q, P, dnum) on one device."""
+
+    def __init__(self, log_n: int, q, p, dnum: int, device: int = 0):
+        self.log_n, self.N = log_n, 1 << log_n
+        self.q, self.p = [int(x) for x in q], [int(x) for x in p]
+        self.L, self.K, self.dnum = len(self.q), len(self.p), dnum
+        self.alpha = -(-self.L // dnum)
+        self.device = device
+        qa = (ctypes.c_uint64 * self.L)(*self.q)
+        pa = (ctypes.c_uint64 * self.K)(*self.p)
+        prm = _Params(log_n, self.L, self.K, dnum, qa, pa)
+        h = ctypes.c_void_p()
+        _check(lib().ckks_context_create(ctypes.byref(prm), device, ctypes.byref(h)), "ckks_context_create")
+        self._h = h
+        self._plans = {}
+
+    @classmethod
+    def from_params(cls, params, device: int = 0) -> "Context":
+        return cls(params.log_n, params.q, params.p, params.dnum, device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for pl in self._plans.values():
+                lib().ckks_plan_destroy(pl)
+            self._plans = {}
+            lib().ckks_context_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ keys
+    def keygen_workspace_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ckks_keygen_workspace_size(self._h, ctypes.byref(n)), "ckks_keygen_workspace_size")
+        return n.value
+
+    def keygen_evk(self, t_max, s, a, e, keys, workspace, stream=None):
+        _check(lib().ckks_keygen_evk(self._h, t_max, s.data_ptr(), a.data_ptr(), e.data_ptr(), keys.data_ptr(),
+                                     workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                     _stream(stream)), "ckks_keygen_evk")
+
+    def evk_set(self, t_max: int, keys, stream=None) -> "EvkSet":
+        h = ctypes.c_void_p()
+        _check(lib().ckks_evk_set_create(self._h, t_max, keys.data_ptr(), _stream(stream), ctypes.byref(h)),
+               "ckks_evk_set_create")
+        return EvkSet(self, h, keys, t_max)
+
+    # ----------------------------------------------------------------- plans
+    def plan(self, k: int, partition: str | None = None):
+        key = (k, partition)
+        if key not in self._plans:
+            h = ctypes.c_void_p()
+            part = partition.encode() if partition else None
+            _check(lib().ckks_plan_create(self._h, k, part, ctypes.byref(h)), f"ckks_plan_create({k}, {partition})")
+            self._plans[key] = h
+        return self._plans[key]
+
+    def plan_describe(self, k: int, partition: str | None = None):
+        d, r, n = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().ckks_plan_describe(self.plan(k, partition), ctypes.byref(d), ctypes.byref(r), ctypes.byref(n)),
+               "ckks_plan_describe")
+        return {"depth": d.value, "rs_units": r.value, "nodes": n.value}
+
+    def workspace_size(self, k: int, level: int, batch: int = 1, partition: str | None = None) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ckks_workspace_size(self._h, self.plan(k, partition), level, batch, ctypes.byref(n)),
+               "ckks_workspace_size")
+        return n.value
+
+    # -------------------------------------------------------------- multiply
+    def mul_k(self, cts, evk, out: Tuple, workspace, partition=None, stream=None) -> Tuple:
+        k = len(cts)
+        arr = (_Tuple * k)(*[c.c() for c in cts])
+        o = out.c()
+        _check(lib().ckks_mul_k(self._h, arr, k, evk._h, self.plan(k, partition), ctypes.byref(o),
+                                workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                _stream(stream)), "ckks_mul_k")
+        out.level, out.n_polys, out.ntt_form, out.scale, out.poly_stride = o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride
+        return out
+
+    def mul_k_batch(self, cts, evk, outs, workspace, partition=None, stream=None):
+        """cts: list over batch of lists of k Tuples (strided views of batched
+        tensors); outs: list over batch of Tuples."""
+        B, k = len(cts), len(cts[0])
+        arr = (_Tuple * (B * k))(*[c.c() for row in cts for c in row])
+        oarr = (_Tuple * B)(*[o.c() for o in outs])
+        _check(lib().ckks_mul_k_batch(self._h, arr, k, B, evk._h, self.plan(k, partition), oarr,
+                                      workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                      _stream(stream)), "ckks_mul_k_batch")
+        for o, r in zip(outs, oarr):
+            o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride = r.level, r.n_polys, r.ntt_form, r.scale, r.poly_stride
+        return outs
+
+    def mul2_workspace_size(self, level: int, batch: int = 1) -> int:
+        v = ctypes.c_size_t()
+        _check(lib().ckks_mul2_workspace_size(self._h, level, batch, ctypes.byref(v)), "ckks_mul2_workspace_size")
+        return v.value
+
+    def mul2_batch(self, a, b, evk, outs, workspace, stream=None):
+        """a, b, outs: lists over the batch of Tuples (evenly strided)."""
+        B = len(a)
+        aa = (_Tuple * B)(*[t.c() for t in a])
+        bb = (_Tuple * B)(*[t.c() for t in b])
+        oo = (_Tuple * B)(*[t.c() for t in outs])
+        _check(lib().ckks_mul2_batch(self._h, aa, bb, B, evk._h, oo, workspace.data_ptr(),
+                                     workspace.numel() * workspace.element_size(), _stream(stream)),
+               "ckks_mul2_batch")
+        for o, r in zip(outs, oo):
+            o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride = r.level, r.n_polys, r.ntt_form, r.scale, r.poly_stride
+        return outs
+
+    def mul2(self, a: Tuple, b: Tuple, evk, out: Tuple, workspace, stream=None) -> Tuple:
+        o = out.c()
+        ca, cb = a.c(), b.c()
+        _check(lib().ckks_mul2(self._h, ctypes.byref(ca), ctypes.byref(cb), evk._h, ctypes.byref(o),
+                               workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream)),
+               "ckks_mul2")
+        out.level, out.n_polys, out.ntt_form, out.scale = o.level, o.n_polys, o.ntt_form, o.scale
+        return out
+
+    # ----------------------------------------------------------------- steps
+    def tensor(self, ins, out: Tuple, stream=None) -> Tuple:
+        arr = (_Tuple * len(ins))(*[t.c() for t in ins])
+        o = out.c()
+        _check(lib().ckks_tensor(self._h, arr, len(ins), ctypes.byref(o), _stream(stream)), "ckks_tensor")
+        out.level, out.n_polys, out.ntt_form, out.scale = o.level, o.n_polys, o.ntt_form, o.scale
+        return out
+
+    def relin_workspace_size(self, n: int, level: int) -> int:
+        v = ctypes.c_size_t()
+        _check(lib().ckks_relin_workspace_size(self._h, n, level, ctypes.byref(v)), "ckks_relin_workspace_size")
+        return v.value
+
+    def relin(self, d: Tuple, evk, out: Tuple, workspace, out_ntt: bool = False, stream=None) -> Tuple:
+        cd, o = d.c(), out.c()
+        _check(lib().ckks_relin(self._h, ctypes.byref(cd), evk._h, int(out_ntt), ctypes.byref(o),
+                                workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                _stream(stream)), "ckks_relin")
+        out.level, out.n_polys, out.ntt_form, out.scale = o.level, o.n_polys, o.ntt_form, o.scale
+        return out
+
+    def rescale_workspace_size(self, n_polys: int, level: int, mu: int) -> int:
+        v = ctypes.c_size_t()
+        _check(lib().ckks_rescale_workspace_size(self._h, n_polys, level, mu, ctypes.byref(v)),
+               "ckks_rescale_workspace_size")
+        return v.value
+
+    def rescale_multi(self, t: Tuple, mu: int, out: Tuple, workspace, stream=None) -> Tuple:
+        ci, o = t.c(), out.c()
+        _check(lib().ckks_rescale_multi(self._h, ctypes.byref(ci), mu, ctypes.byref(o), workspace.data_ptr(),
+                                        workspace.numel() * workspace.element_size(), _stream(stream)),
+               "ckks_rescale_multi")
+        out.level, out.n_polys, out.ntt_form, out.scale, out.poly_stride = o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride
+        return out
+
+    def ntt(self, t: Tuple, out: Tuple | None = None, stream=None) -> Tuple:
+        out = out or t
+        ci, o = t.c(), out.c()
+        _check(lib().ckks_ntt(self._h, ctypes.byref(ci), ctypes.byref(o), _stream(stream)), "ckks_ntt")
+        out.level, out.n_polys, out.ntt_form = o.level, o.n_polys, o.ntt_form
+        return out
+
+    def intt(self, t: Tuple, out: Tuple | None = None, stream=None) -> Tuple:
+        out = out or t
+        ci, o = t.c(), out.c()
+        _check(lib().ckks_intt(self._h, ctypes.byref(ci), ctypes.byref(o), _stream(stream)), "ckks_intt")
+        out.level, out.n_polys, out.ntt_form = o.level, o.n_polys, o.ntt_form
+        return out
+
+    # ---------------------------------------------------------------- status
+    def counters(self, reset: bool = False) -> dict:
+        c = _Counters()
+        _check(lib().ckks_counters(self._h, ctypes.byref(c), int(reset)), "ckks_counters")
+        return {n: getattr(c, n) for n, _ in _Counters._fields_}
+
+    def check(self):
+        _check(lib().ckks_check(self._h), "ckks_check")
+
+    def profile(self, enable: bool):
+        _check(lib().ckks_profile_enable(self._h, int(enable)), "ckks_profile_enable")
+
+    def profile_read(self) -> dict:
+        arr = (_KStats * 16)()
+        n = ctypes.c_uint32()
+        _check(lib().ckks_profile_read(self._h, arr, 16, ctypes.byref(n)), "ckks_profile_read")
+        return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms,
+                                       "alg_bytes": arr[i].alg_bytes} for i in range(n.value)}
+
+
+class EvkSet:
+    def __init__(self, ctx: Context, h, keys, t_max: int):
+        self.ctx, self._h, self.keys, self.t_max = ctx, h, keys, t_max
+
+    def close(self):
+        if self._h:
+            lib().ckks_evk_set_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,72 @@
+"""Loading libckks_mulk.so and declaring the C ABI of include/ckks_mulk.h."""
+from __future__ import annotations
+
+import ctypes
+import os
+from functools import lru_cache
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+ERRORS = {0: "CKKS_OK", -1: "CKKS_EINVAL", -2: "CKKS_ELEVEL", -3: "CKKS_EKEY", -4: "CKKS_ENOMEM",
+          -5: "CKKS_ECUDA", -6: "CKKS_ETIMEOUT", -7: "CKKS_EBUSY"}
+
+
+class CkksError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(msg)
+        self.code = code
+
+
+def library_path() -> str:
+    return os.environ.get("CKKS_MULK_LIB", os.path.join(_HERE, "libckks_mulk.so"))
+
+
+V, P, I, U32, SZ, D = (ctypes.c_void_p, ctypes.POINTER, ctypes.c_int, ctypes.c_uint32, ctypes.c_size_t,
+                       ctypes.c_double)
+
+# name -> argument types (return type int unless listed in _VOID / _STR)
+SIGNATURES = {
+    "ckks_context_create": [V, I, V],
+    "ckks_context_destroy": [V],
+    "ckks_keygen_workspace_size": [V, V],
+    "ckks_keygen_evk": [V, U32, V, V, V, V, V, SZ, V],
+    "ckks_evk_set_create": [V, U32, V, V, V],
+    "ckks_evk_set_destroy": [V],
+    "ckks_plan_create": [V, U32, ctypes.c_char_p, V],
+    "ckks_plan_destroy": [V],
+    "ckks_plan_describe": [V, V, V, V],
+    "ckks_workspace_size": [V, V, U32, U32, V],
+    "ckks_mul_k": [V, V, U32, V, V, V, V, SZ, V],
+    "ckks_mul_k_batch": [V, V, U32, U32, V, V, V, V, SZ, V],
+    "ckks_mul2_workspace_size": [V, U32, U32, V],
+    "ckks_mul2": [V, V, V, V, V, V, SZ, V],
+    "ckks_mul2_batch": [V, V, V, U32, V, V, V, SZ, V],
+    "ckks_tensor": [V, V, U32, V, V],
+    "ckks_relin_workspace_size": [V, U32, U32, V],
+    "ckks_relin": [V, V, V, U32, V, V, SZ, V],
+    "ckks_rescale_workspace_size": [V, U32, U32, U32, V],
+    "ckks_rescale_multi": [V, V, U32, V, V, SZ, V],
+    "ckks_ntt": [V, V, V, V],
+    "ckks_intt": [V, V, V, V],
+    "ckks_counters": [V, V, I],
+    "ckks_check": [V],
+    "ckks_profile_enable": [V, I],
+    "ckks_profile_read": [V, V, U32, V],
+    "ckks_strerror": [I],
+}
+_VOID = {"ckks_context_destroy", "ckks_evk_set_destroy", "ckks_plan_destroy"}
+_STR = {"ckks_strerror"}
+
+
+@lru_cache(maxsize=1)
+def lib() -> ctypes.CDLL:
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libckks_mulk.so not built ({path}); run __graft_entry__.build() or "
+                          "python -m paper_2601_15401_gb300.build")
+    L = ctypes.CDLL(path)
+    for name, args in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = None if name in _VOID else (ctypes.c_char_p if name in _STR else ctypes.c_int)
+    return L

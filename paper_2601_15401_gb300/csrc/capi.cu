@@ -1,0 +1,512 @@
+// extern "C" entry points declared in include/ckks_mulk.h: argument checks,
+// tuple -> view marshalling, error codes. No exception crosses the ABI.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "../../include/ckks_mulk.h"
+#include "engine.h"
+#include "internal.h"
+#include "plan.h"
+#include "rns.h"
+
+using namespace ckks;
+
+struct ckks_context {
+    Context c;
+};
+struct ckks_evk_set {
+    ckks_context *ctx;
+    u64 *keys;
+    uint32_t t_max;
+};
+struct ckks_plan {
+    Plan p;
+};
+
+static int cuda_fail(ckks_context *ctx, cudaError_t e) {
+    if (e != cudaSuccess) {
+        ctx->c.sticky.store((int)e);
+        return CKKS_ECUDA;
+    }
+    return CKKS_OK;
+}
+
+static int finish(ckks_context *ctx, int rc, cudaError_t e) {
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    return rc;
+}
+
+static bool tuple_ok(const ckks_tuple *t, uint32_t L) {
+    return t && t->data && t->level >= 1 && t->level <= L && t->poly_stride >= t->level && t->n_polys >= 1 &&
+           t->n_polys <= CKKS_MAX_TUPLE;
+}
+
+static LimbView tview(const ckks_tuple &t, int N, i64 bstride = 0) {
+    LimbView v;
+    v.ptr = (u64 *)t.data;
+    v.bstride = bstride;
+    v.pstride = (i64)t.poly_stride * N;
+    return v;
+}
+
+static cudaStream_t S(void *s) { return (cudaStream_t)s; }
+
+extern "C" {
+
+int ckks_context_create(const ckks_params *params, int device, ckks_context **out) {
+    if (!params || !out || !params->q || !params->p) return CKKS_EINVAL;
+    *out = nullptr;
+    ckks_context *ctx = new (std::nothrow) ckks_context();
+    if (!ctx) return CKKS_ENOMEM;
+    int rc = context_build(ctx->c, params->log_n, params->L, params->K, params->dnum, (const u64 *)params->q,
+                           (const u64 *)params->p, device);
+    if (rc != 0) {
+        context_release(ctx->c);
+        delete ctx;
+        return rc == -5 ? CKKS_ECUDA : CKKS_EINVAL;
+    }
+    *out = ctx;
+    return CKKS_OK;
+}
+
+void ckks_context_destroy(ckks_context *ctx) {
+    if (!ctx) return;
+    context_release(ctx->c);
+    delete ctx;
+}
+
+int ckks_keygen_workspace_size(const ckks_context *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return CKKS_EINVAL;
+    *bytes = (size_t)3 * (ctx->c.L + ctx->c.K) * ctx->c.N * sizeof(u64);
+    return CKKS_OK;
+}
+
+int ckks_keygen_evk(ckks_context *ctx, uint32_t t_max, const int64_t *s, const uint64_t *a, const int64_t *e,
+                    uint64_t *keys, void *workspace, size_t ws_bytes, void *stream) {
+    if (!ctx || !s || !a || !e || !keys || !workspace || t_max < 2 || t_max > 13) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    size_t need;
+    ckks_keygen_workspace_size(ctx, &need);
+    if (ws_bytes < need) return CKKS_ENOMEM;
+    cudaSetDevice(C.device);
+    const int NP = C.L + C.K;
+    const size_t plane = (size_t)NP * C.N;
+    u64 *Sb = (u64 *)workspace, *St = Sb + plane, *E = St + plane;
+    cudaStream_t st = S(stream);
+    LimbView v = {Sb, 0, (i64)plane};
+    cudaError_t err = launch_signed_to_res(C, (const long long *)s, Sb, st);
+    if (err == cudaSuccess) {
+        LimbJobs J;
+        memset(&J, 0, sizeof(J));
+        J.n_batch = 1;
+        J.n_polys = 1;
+        J.n_limbs = NP;
+        for (int i = 0; i < NP; ++i) J.slot[i] = J.dslot[i] = J.prime[i] = (uint8_t)i;
+        LoadSpec L{};
+        L.mode = LD_PLAIN;
+        L.a = v;
+        StoreSpec Sp{};
+        Sp.mode = ST_REDUCE;
+        Sp.dst = v;
+        err = ntt_transform(C, true, J, L, Sp, nullptr, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(St, Sb, plane * sizeof(u64), cudaMemcpyDeviceToDevice, st);
+        for (uint32_t t = 2; t <= t_max && err == cudaSuccess; ++t) {
+            err = launch_pointwise_mul(C, St, Sb, st);
+            for (int b = 0; b < C.dnum && err == cudaSuccess; ++b) {
+                const size_t kb = (size_t)(t - 2) * C.dnum + b;
+                err = launch_signed_to_res(C, (const long long *)(e + kb * C.N), E, st);
+                if (err != cudaSuccess) break;
+                LoadSpec Le{};
+                Le.mode = LD_PLAIN;
+                Le.a = LimbView{E, 0, (i64)plane};
+                StoreSpec Se{};
+                Se.mode = ST_REDUCE;
+                Se.dst = Le.a;
+                err = ntt_transform(C, true, J, Le, Se, nullptr, st);
+                if (err != cudaSuccess) break;
+                err = launch_keygen(C, Sb, St, E, (const u64 *)a + kb * plane, (u64 *)keys + kb * 2 * plane, b, st);
+            }
+        }
+    }
+    return finish(ctx, CKKS_OK, err);
+}
+
+int ckks_evk_set_create(ckks_context *ctx, uint32_t t_max, uint64_t *keys, void *stream, ckks_evk_set **out) {
+    if (!ctx || !keys || !out || t_max < 2 || t_max > 13) return CKKS_EINVAL;
+    *out = nullptr;
+    const Context &C = ctx->c;
+    cudaSetDevice(C.device);
+    long long rows = (long long)(t_max - 1) * C.dnum * 2 * (C.L + C.K);
+    cudaError_t err = launch_keyprep(C, (u64 *)keys, rows, S(stream));
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    ckks_evk_set *set = new (std::nothrow) ckks_evk_set{ctx, (u64 *)keys, t_max};
+    if (!set) return CKKS_ENOMEM;
+    *out = set;
+    return CKKS_OK;
+}
+
+void ckks_evk_set_destroy(ckks_evk_set *set) { delete set; }
+
+int ckks_plan_create(ckks_context *ctx, uint32_t k, const char *partition, ckks_plan **out) {
+    (void)ctx;
+    if (!out) return CKKS_EINVAL;
+    *out = nullptr;
+    ckks_plan *p = new (std::nothrow) ckks_plan();
+    if (!p) return CKKS_ENOMEM;
+    if (plan_build(p->p, (int)k, partition) != 0) {
+        delete p;
+        return CKKS_EINVAL;
+    }
+    *out = p;
+    return CKKS_OK;
+}
+
+void ckks_plan_destroy(ckks_plan *plan) { delete plan; }
+
+int ckks_plan_describe(const ckks_plan *plan, uint32_t *depth, uint32_t *rs_units, uint32_t *n_nodes) {
+    if (!plan) return CKKS_EINVAL;
+    if (depth) *depth = (uint32_t)plan->p.depth;
+    if (rs_units) *rs_units = (uint32_t)plan->p.rs_units;
+    if (n_nodes) *n_nodes = (uint32_t)plan->p.nodes.size();
+    return CKKS_OK;
+}
+
+int ckks_workspace_size(const ckks_context *ctx, const ckks_plan *plan, uint32_t level, uint32_t batch,
+                        size_t *bytes) {
+    if (!ctx || !plan || !bytes || batch < 1) return CKKS_EINVAL;
+    if (level > (uint32_t)ctx->c.L || (int)level <= plan->p.depth) return CKKS_ELEVEL;
+    *bytes = mul_k_ws_bytes(ctx->c, plan->p, (int)level, (int)batch);
+    return CKKS_OK;
+}
+
+// scale of the result: product of input scales / primes divided at each node
+static double plan_scale(const Context &C, const Plan &P, int level, const double *scales) {
+    std::vector<int> lin, lout, polys;
+    plan_levels(P, level, lin, lout, polys);
+    std::vector<double> sc(P.nodes.size(), 1.0);
+    for (size_t i = 0; i < P.nodes.size(); ++i) {
+        double s = 1.0;
+        for (int c : P.nodes[i].children) s *= c >= 0 ? sc[c] : scales[-1 - c];
+        for (int j = 0; j < P.nodes[i].mu; ++j) s /= (double)C.primes[lin[i] - 1 - j];
+        sc[i] = s;
+    }
+    return sc.back();
+}
+
+static int mul_k_common(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uint32_t batch, const ckks_evk_set *evk,
+                        const ckks_plan *plan, ckks_tuple *out, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !ct || !evk || !plan || !out || batch < 1) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    const Plan &P = plan->p;
+    if ((int)k != P.k || evk->ctx != ctx) return CKKS_EINVAL;
+    const uint32_t level = ct[0].level;
+    for (uint32_t i = 0; i < k * batch; ++i) {
+        const ckks_tuple &t = ct[i];
+        if (!tuple_ok(&t, C.L) || t.n_polys != 2 || t.ntt_form != 1 || t.level != level ||
+            t.poly_stride != ct[i % k].poly_stride)
+            return CKKS_EINVAL;
+    }
+    if ((int)level <= P.depth) return CKKS_ELEVEL;
+    if (evk->t_max < k) return CKKS_EKEY;
+    const uint32_t out_level = level - P.depth;
+    std::vector<LimbView> in(k);
+    for (uint32_t u = 0; u < k; ++u) {
+        i64 bs = 0;
+        if (batch > 1) bs = (i64)(ct[k + u].data - ct[u].data);
+        for (uint32_t b = 0; b < batch; ++b)
+            if (ct[b * k + u].data != ct[u].data + b * bs) return CKKS_EINVAL;
+        in[u] = tview(ct[u], C.N, bs);
+    }
+    for (uint32_t b = 0; b < batch; ++b) {
+        if (!out[b].data) return CKKS_EINVAL;
+        if (out[b].poly_stride == 0) out[b].poly_stride = out_level;
+        if (out[b].poly_stride < out_level || out[b].poly_stride != out[0].poly_stride) return CKKS_EINVAL;
+    }
+    i64 obs = batch > 1 ? (i64)(out[1].data - out[0].data) : 0;
+    for (uint32_t b = 0; b < batch; ++b)
+        if (out[b].data != out[0].data + b * obs) return CKKS_EINVAL;
+    size_t need = mul_k_ws_bytes(C, P, (int)level, (int)batch);
+    if (!ws || ws_bytes < need) return CKKS_ENOMEM;
+    cudaSetDevice(C.device);
+    cudaError_t err;
+    int rc = run_mul_k_ws(C, P, (int)level, (int)batch, in.data(), tview(out[0], C.N, obs), evk->keys,
+                          (int)evk->t_max, ws, ws_bytes, S(stream), err);
+    if (rc == -3) return CKKS_EKEY;
+    if (err != cudaSuccess || rc != 0) return cuda_fail(ctx, err == cudaSuccess ? cudaErrorUnknown : err);
+    for (uint32_t b = 0; b < batch; ++b) {
+        std::vector<double> sc(k);
+        for (uint32_t u = 0; u < k; ++u) sc[u] = ct[b * k + u].scale;
+        out[b].n_polys = 2;
+        out[b].level = out_level;
+        out[b].ntt_form = 1;
+        out[b].scale = plan_scale(C, P, (int)level, sc.data());
+    }
+    return CKKS_OK;
+}
+
+int ckks_mul_k(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, const ckks_evk_set *evk, const ckks_plan *plan,
+               ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream) {
+    return mul_k_common(ctx, ct, k, 1, evk, plan, out, workspace, ws_bytes, stream);
+}
+
+int ckks_mul_k_batch(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uint32_t batch, const ckks_evk_set *evk,
+                     const ckks_plan *plan, ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream) {
+    return mul_k_common(ctx, ct, k, batch, evk, plan, out, workspace, ws_bytes, stream);
+}
+
+// batch stride of a [batch] tuple array; -1 if the pointers are not evenly spaced
+static i64 batch_stride(const ckks_tuple *t, uint32_t batch) {
+    i64 bs = batch > 1 ? (i64)(t[1].data - t[0].data) : 0;
+    for (uint32_t b = 0; b < batch; ++b)
+        if (t[b].data != t[0].data + b * bs) return -1;
+    return bs;
+}
+
+int ckks_mul2_workspace_size(const ckks_context *ctx, uint32_t level, uint32_t batch, size_t *bytes) {
+    if (!ctx || !bytes || batch < 1) return CKKS_EINVAL;
+    if (level < 2 || level > (uint32_t)ctx->c.L) return CKKS_ELEVEL;
+    *bytes = mul2_ws_bytes(ctx->c, (int)level, (int)batch);
+    return CKKS_OK;
+}
+
+int ckks_mul2_batch(ckks_context *ctx, const ckks_tuple *a, const ckks_tuple *b, uint32_t batch,
+                    const ckks_evk_set *evk, ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream) {
+    if (!ctx || !a || !b || !evk || !out || evk->ctx != ctx || batch < 1) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    for (uint32_t i = 0; i < batch; ++i) {
+        if (!tuple_ok(&a[i], C.L) || !tuple_ok(&b[i], C.L) || a[i].n_polys != 2 || b[i].n_polys != 2 ||
+            !a[i].ntt_form || !b[i].ntt_form || !out[i].data || a[i].level != a[0].level ||
+            b[i].level != b[0].level || a[i].poly_stride != a[0].poly_stride ||
+            b[i].poly_stride != b[0].poly_stride)
+            return CKKS_EINVAL;
+    }
+    const int level = (int)std::min(a[0].level, b[0].level);
+    if (level < 2) return CKKS_ELEVEL;
+    if (evk->t_max < 2) return CKKS_EKEY;
+    for (uint32_t i = 0; i < batch; ++i) {
+        if (out[i].poly_stride == 0) out[i].poly_stride = level - 1;
+        if ((int)out[i].poly_stride < level - 1 || out[i].poly_stride != out[0].poly_stride) return CKKS_EINVAL;
+    }
+    i64 as = batch_stride(a, batch), bs = batch_stride(b, batch), os = batch_stride(out, batch);
+    if (as < 0 || bs < 0 || os < 0) return CKKS_EINVAL;
+    size_t need = mul2_ws_bytes(C, level, (int)batch);
+    if (!workspace || ws_bytes < need) return CKKS_ENOMEM;
+    cudaSetDevice(C.device);
+    cudaError_t err;
+    int rc = run_mul2_ws(C, level, (int)batch, tview(a[0], C.N, as), tview(b[0], C.N, bs), tview(out[0], C.N, os),
+                         evk->keys, workspace, ws_bytes, S(stream), err);
+    if (err != cudaSuccess || rc != 0) return cuda_fail(ctx, err == cudaSuccess ? cudaErrorUnknown : err);
+    for (uint32_t i = 0; i < batch; ++i) {
+        out[i].n_polys = 2;
+        out[i].level = level - 1;
+        out[i].ntt_form = 1;
+        out[i].scale = a[i].scale * b[i].scale / (double)C.primes[level - 1];
+    }
+    return CKKS_OK;
+}
+
+int ckks_mul2(ckks_context *ctx, const ckks_tuple *a, const ckks_tuple *b, const ckks_evk_set *evk, ckks_tuple *out,
+              void *workspace, size_t ws_bytes, void *stream) {
+    return ckks_mul2_batch(ctx, a, b, 1, evk, out, workspace, ws_bytes, stream);
+}
+
+int ckks_tensor(ckks_context *ctx, const ckks_tuple *in, uint32_t m, ckks_tuple *out, void *stream) {
+    if (!ctx || !in || !out || !out->data || m < 1 || m > CKKS_MAX_CHILDREN) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    uint32_t level = 1u << 30, np = 1;
+    std::vector<LimbView> v(m);
+    std::vector<int> polys(m);
+    double scale = 1.0;
+    for (uint32_t i = 0; i < m; ++i) {
+        if (!tuple_ok(&in[i], C.L) || !in[i].ntt_form) return CKKS_EINVAL;
+        level = std::min(level, in[i].level);
+        np += in[i].n_polys - 1;
+        v[i] = tview(in[i], C.N);
+        polys[i] = (int)in[i].n_polys;
+        scale *= in[i].scale;
+    }
+    if (np > CKKS_MAX_TUPLE) return CKKS_EINVAL;
+    if (out->poly_stride == 0) out->poly_stride = level;
+    if (out->poly_stride < level) return CKKS_EINVAL;
+    cudaSetDevice(C.device);
+    cudaError_t err = run_tensor(C, 1, (int)level, (int)m, v.data(), polys.data(), tview(*out, C.N), S(stream));
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    out->n_polys = np;
+    out->level = level;
+    out->ntt_form = 1;
+    out->scale = scale;
+    return CKKS_OK;
+}
+
+int ckks_relin_workspace_size(const ckks_context *ctx, uint32_t n, uint32_t level, size_t *bytes) {
+    if (!ctx || !bytes || n < 2 || level < 1 || level > (uint32_t)ctx->c.L) return CKKS_EINVAL;
+    *bytes = relin_ws_bytes(ctx->c, (int)n, (int)level, 1);
+    return CKKS_OK;
+}
+
+int ckks_relin(ckks_context *ctx, const ckks_tuple *d, const ckks_evk_set *evk, uint32_t out_ntt, ckks_tuple *out,
+               void *workspace, size_t ws_bytes, void *stream) {
+    if (!ctx || !d || !evk || !out || !out->data || evk->ctx != ctx) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    if (!tuple_ok(d, C.L) || d->n_polys < 3 || !d->ntt_form) return CKKS_EINVAL;
+    const uint32_t n = d->n_polys - 1;
+    if (evk->t_max < n) return CKKS_EKEY;
+    if (out->poly_stride == 0) out->poly_stride = d->level;
+    if (out->poly_stride < d->level) return CKKS_EINVAL;
+    size_t need = relin_ws_bytes(C, (int)n, (int)d->level, 1);
+    if (!workspace || ws_bytes < need) return CKKS_ENOMEM;
+    cudaSetDevice(C.device);
+    cudaError_t err;
+    int rc = run_relin_ws(C, 1, (int)n, (int)d->level, tview(*d, C.N), evk->keys, out_ntt != 0, tview(*out, C.N),
+                          workspace, ws_bytes, S(stream), err);
+    if (err != cudaSuccess || rc != 0) return cuda_fail(ctx, err == cudaSuccess ? cudaErrorUnknown : err);
+    out->n_polys = 2;
+    out->level = d->level;
+    out->ntt_form = out_ntt ? 1 : 0;
+    out->scale = d->scale;
+    return CKKS_OK;
+}
+
+int ckks_rescale_workspace_size(const ckks_context *ctx, uint32_t n_polys, uint32_t level, uint32_t mu,
+                                size_t *bytes) {
+    if (!ctx || !bytes || mu < 1 || mu >= level || level > (uint32_t)ctx->c.L || n_polys < 1) return CKKS_EINVAL;
+    *bytes = rescale_ws_bytes(ctx->c, (int)n_polys, (int)level, (int)mu, 1);
+    return CKKS_OK;
+}
+
+int ckks_rescale_multi(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckks_tuple *out, void *workspace,
+                       size_t ws_bytes, void *stream) {
+    if (!ctx || !in || !out || !out->data) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    if (!tuple_ok(in, C.L) || !in->ntt_form) return CKKS_EINVAL;
+    if (mu < 1 || mu >= in->level) return CKKS_ELEVEL;
+    const uint32_t ol = in->level - mu;
+    if (out->poly_stride == 0) out->poly_stride = out->data == in->data ? in->poly_stride : ol;
+    if (out->poly_stride < ol) return CKKS_EINVAL;
+    if (out->data == in->data && out->poly_stride != in->poly_stride) return CKKS_EINVAL;
+    size_t need = rescale_ws_bytes(C, (int)in->n_polys, (int)in->level, (int)mu, 1);
+    if (!workspace || ws_bytes < need) return CKKS_ENOMEM;
+    cudaSetDevice(C.device);
+    cudaError_t err;
+    double scale = in->scale;
+    for (uint32_t j = 0; j < mu; ++j) scale /= (double)C.primes[in->level - 1 - j];
+    uint32_t np = in->n_polys;
+    int rc = run_rescale_ws(C, 1, (int)np, (int)in->level, (int)mu, tview(*in, C.N), tview(*out, C.N), workspace,
+                            ws_bytes, S(stream), err);
+    if (err != cudaSuccess || rc != 0) return cuda_fail(ctx, err == cudaSuccess ? cudaErrorUnknown : err);
+    out->n_polys = np;
+    out->level = ol;
+    out->ntt_form = 1;
+    out->scale = scale;
+    return CKKS_OK;
+}
+
+static int transform_api(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *stream, bool fwd) {
+    if (!ctx || !in || !out || !out->data) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    if (!tuple_ok(in, C.L)) return CKKS_EINVAL;
+    if (out->poly_stride == 0) out->poly_stride = in->poly_stride;
+    if (out->poly_stride < in->level) return CKKS_EINVAL;
+    cudaSetDevice(C.device);
+    cudaError_t err = transform_plain(C, fwd, 1, (int)in->n_polys, (int)in->level, tview(*in, C.N),
+                                      tview(*out, C.N), S(stream));
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    out->n_polys = in->n_polys;
+    out->level = in->level;
+    out->ntt_form = fwd ? 1 : 0;
+    out->scale = in->scale;
+    return CKKS_OK;
+}
+
+int ckks_ntt(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *stream) {
+    return transform_api(ctx, in, out, stream, true);
+}
+
+int ckks_intt(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *stream) {
+    return transform_api(ctx, in, out, stream, false);
+}
+
+int ckks_counters(ckks_context *ctx, ckks_op_counters *out, int reset) {
+    if (!ctx || !out) return CKKS_EINVAL;
+    Context &C = ctx->c;
+    out->limb_ntt = C.counters[OP_LIMB_NTT].load();
+    out->limb_intt = C.counters[OP_LIMB_INTT].load();
+    out->ntt_phase = C.counters[OP_NTT_PHASE].load();
+    out->intt_phase = C.counters[OP_INTT_PHASE].load();
+    out->bconv = C.counters[OP_BCONV].load();
+    out->kernels = C.counters[OP_KERNELS].load();
+    if (reset)
+        for (int i = 0; i < OP_COUNT; ++i) C.counters[i] = 0;
+    return CKKS_OK;
+}
+
+static const char *kClassNames[KC_COUNT] = {"ntt_fwd_cols", "ntt_fwd_blocks", "ntt_inv_blocks", "ntt_inv_cols",
+                                            "tensor",       "bconv",          "key_mac",        "rs_chain",
+                                            "keys"};
+
+int ckks_profile_enable(ckks_context *ctx, int enable) {
+    if (!ctx) return CKKS_EINVAL;
+    Profiler &P = ctx->c.prof;
+    if (enable) {
+        P.recs.clear();
+        P.used = 0;
+    }
+    P.on = enable != 0;
+    return CKKS_OK;
+}
+
+int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, uint32_t *n_out) {
+    if (!ctx || !out || !n_out) return CKKS_EINVAL;
+    cudaSetDevice(ctx->c.device);
+    double ms[KC_COUNT] = {0}, by[KC_COUNT] = {0};
+    uint64_t cnt[KC_COUNT] = {0};
+    for (const ProfRec &r : ctx->c.prof.recs) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return CKKS_ECUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return CKKS_ECUDA;
+        ms[r.cls] += t;
+        by[r.cls] += r.bytes;
+        cnt[r.cls] += 1;
+    }
+    uint32_t n = 0;
+    for (int c = 0; c < KC_COUNT && n < max; ++c) {
+        if (!cnt[c]) continue;
+        memset(&out[n], 0, sizeof(out[n]));
+        strncpy(out[n].name, kClassNames[c], sizeof(out[n].name) - 1);
+        out[n].launches = cnt[c];
+        out[n].total_ms = ms[c];
+        out[n].alg_bytes = by[c];
+        ++n;
+    }
+    *n_out = n;
+    return CKKS_OK;
+}
+
+int ckks_check(ckks_context *ctx) {
+    if (!ctx) return CKKS_EINVAL;
+    if (ctx->c.sticky.load() != 0) return CKKS_ECUDA;
+    cudaSetDevice(ctx->c.device);
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        ctx->c.sticky.store((int)e);
+        return CKKS_ECUDA;
+    }
+    return CKKS_OK;
+}
+
+const char *ckks_strerror(int code) {
+    switch (code) {
+    case CKKS_OK: return "ok";
+    case CKKS_EINVAL: return "invalid argument";
+    case CKKS_ELEVEL: return "level too low for the partition depth, or above L";
+    case CKKS_EKEY: return "evaluation-key set lacks a needed ek_t";
+    case CKKS_ENOMEM: return "workspace too small";
+    case CKKS_ECUDA: return "CUDA error";
+    case CKKS_ETIMEOUT: return "device wait timed out";
+    case CKKS_EBUSY: return "admission refused";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

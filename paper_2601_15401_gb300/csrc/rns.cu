@@ -1,0 +1,332 @@
+// Coefficient-wise RNS kernels of the k-input multiplication:
+//   tensor product of child tuples (Eq. 1, 8, 13), fast basis conversion for
+//   ModUp (Eq. 4), the evaluation-key inner product summed over every key
+//   and digit before one ModDown (Eq. 15 and the combined form of
+//   Section III), the rescale chain among the top limbs (Eq. 6, Algorithm 1
+//   step 2), key preparation (P^-1 folded into the Q limbs, Eq. 12) and key
+//   generation (Eq. 2, 9, 14).
+//
+// All are memory-bound streams over [batch][poly][limb][N]; each thread owns
+// one coefficient and loops over what the formula sums, keeping partial sums
+// in 128-bit accumulators reduced once (Montgomery REDC).
+#include "common.cuh"
+#include "internal.h"
+#include "rns.h"
+
+namespace ckks {
+
+static constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// tensor product: out = prod over children of (sum_l c_l s^l), coefficient-
+// wise in the NTT domain. Each child product is a Montgomery product, so the
+// result carries R^-(m-1); the final multiply by R^m (REDC) removes it.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 per_b = (i64)A.level * A.N;
+    if (gid >= per_b * A.n_batch) return;
+    const int b = (int)(gid / per_b);
+    const i64 r = gid % per_b;
+    const int j = (int)(r / A.N);
+    const int e = (int)(r % A.N);
+    const ModQ m = A.mods[j];
+    const u64 q = m.q;
+    u64 cur[CKKS_MAX_TUPLE];
+    int ncur = A.child_polys[0];
+    {
+        const u64 *src = A.child[0].ptr + (i64)b * A.child[0].bstride + (i64)j * A.N + e;
+#pragma unroll
+        for (int a = 0; a < CKKS_MAX_TUPLE; ++a)
+            cur[a] = a < ncur ? src[(i64)a * A.child[0].pstride] : 0ull;
+    }
+    for (int c = 1; c < A.m; ++c) {
+        const int ny = A.child_polys[c];
+        const u64 *src = A.child[c].ptr + (i64)b * A.child[c].bstride + (i64)j * A.N + e;
+        u64 y[CKKS_MAX_TUPLE];
+#pragma unroll
+        for (int a = 0; a < CKKS_MAX_TUPLE; ++a) y[a] = a < ny ? src[(i64)a * A.child[c].pstride] : 0ull;
+        u64 nxt[CKKS_MAX_TUPLE];
+#pragma unroll
+        for (int t = 0; t < CKKS_MAX_TUPLE; ++t) {
+            Acc128 acc;
+            acc.zero();
+#pragma unroll
+            for (int a = 0; a <= t; ++a) {
+                if (a < ncur && t - a < ny) acc.mac(cur[a], y[t - a], q);
+            }
+            nxt[t] = redc(acc.hi, acc.lo, m);
+        }
+        ncur = ncur + ny - 1;
+#pragma unroll
+        for (int t = 0; t < CKKS_MAX_TUPLE; ++t) cur[t] = nxt[t];
+    }
+    const u64 fix = A.rpow[(i64)j * 16 + A.m];  // R^m
+    u64 *dst = A.out.ptr + (i64)b * A.out.bstride + (i64)j * A.N + e;
+#pragma unroll
+    for (int t = 0; t < CKKS_MAX_TUPLE; ++t)
+        if (t < ncur) dst[(i64)t * A.out.pstride] = mont_mul(cur[t], fix, m);
+}
+
+cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st) {
+    i64 total = (i64)A.n_batch * A.level * A.N;
+    int blocks = (int)((total + kThreads - 1) / kThreads);
+    count_kernel(C);
+    int in_polys = 0;
+    for (int c = 0; c < A.m; ++c) in_polys += A.child_polys[c];
+    int out_polys = in_polys - A.m + 1;
+    ProfScope ps(C, KC_TENSOR, (double)(in_polys + out_polys) * A.n_batch * A.level * A.N * sizeof(u64), st);
+    tensor_kernel<<<blocks, kThreads, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// ModUp basis conversion (Eq. 4), coefficient domain:
+//   ext[x] = sum_{j in digit} y'_j [(Q_beta / q_j) mod x]   (mod x)
+// y'_j = [y_j (Q_beta/q_j)^-1]_{q_j} was produced by the INTT's epilogue.
+// blockIdx.y = (t, beta) job, blockIdx.z = batch.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) bconv_kernel(BconvArgs A) {
+    extern __shared__ u64 cs[];  // [alpha][n_targets] Montgomery constants
+    const int job = blockIdx.y;
+    const int b = blockIdx.z;
+    const int t = job / A.n_digits;
+    const int beta = job % A.n_digits;
+    const int d0 = beta * A.alpha;
+    int d1 = d0 + A.alpha;
+    if (d1 > A.level) d1 = A.level;
+    const int na = d1 - d0;
+    // targets: Q limbs outside the digit, then every P limb
+    const int nq_t = A.level - na;
+    const int n_t = nq_t + A.K;
+    const u64 *ctab = A.consts + (i64)beta * A.alpha * A.n_primes;
+    for (int i = threadIdx.x; i < na * n_t; i += blockDim.x) {
+        int jj = i / n_t, ti = i % n_t;
+        int x = ti < nq_t ? (ti < d0 ? ti : ti + na) : A.L + (ti - nq_t);
+        cs[i] = ctab[(i64)jj * A.n_primes + x];
+    }
+    __syncthreads();
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.N) return;
+    const u64 *ysrc = A.y.ptr + (i64)b * A.y.bstride + (i64)t * A.y.pstride + e;
+    u64 y[16];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) y[jj] = jj < na ? ysrc[(i64)(d0 + jj) * A.N] : 0ull;
+    u64 *dst = A.ext.ptr + (i64)b * A.ext.bstride + (i64)(t * A.n_digits + beta) * A.ext.pstride + e;
+    for (int ti = 0; ti < n_t; ++ti) {
+        const int slot = ti < nq_t ? (ti < d0 ? ti : ti + na) : A.level + (ti - nq_t);
+        const int x = ti < nq_t ? slot : A.L + (ti - nq_t);
+        const ModQ m = A.mods[x];
+        Acc128 acc;
+        acc.zero();
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+            if (jj < na) acc.mac(y[jj], cs[jj * n_t + ti], m.q);
+        dst[(i64)slot * A.N] = redc(acc.hi, acc.lo, m);
+    }
+}
+
+cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) {
+    dim3 grid((A.N + kThreads - 1) / kThreads, A.n_t * A.n_digits, A.n_batch);
+    size_t smem = (size_t)A.alpha * (A.level + A.K) * sizeof(u64);
+    count_kernel(C);
+    count_op(C, OP_BCONV, (unsigned long long)A.n_t * A.n_digits * A.n_batch);
+    // reads y' once, writes level + K - |digit| limbs per (t, digit)
+    double limbs_out = (double)A.n_t * ((double)A.n_digits * (A.level + A.K) - A.level);
+    ProfScope ps(C, KC_BCONV, ((double)A.n_t * A.level + limbs_out) * A.n_batch * A.N * sizeof(u64), st);
+    bconv_kernel<<<grid, kThreads, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Key inner product summed over every extra key t = 2..n and digit beta
+// (Eq. 15 combined before ModDown):
+//   acc_l[x] = sum_t sum_beta term(t, beta, x) * ek'_{t,beta,l}[x]
+// term = d_t[x] when x lies in digit beta (the digit's own limbs), else the
+// ModUp output. Keys are in Montgomery form, so one REDC per output.
+// Grid: x = coefficient chunk, y = target limb, z = batch (fastest-varying
+// batch would reuse key tiles in L2; see launch order below).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) mac_kernel(MacArgs A) {
+    const int chunks = (A.N + kThreads - 1) / kThreads;
+    // block order: batch fastest, then chunk, then limb -> blocks that share a
+    // key tile run next to each other
+    int bid = blockIdx.x;
+    const int b = bid % A.n_batch;
+    bid /= A.n_batch;
+    const int chunk = bid % chunks;
+    const int x = bid / chunks;  // acc slot: Q limbs 0..level-1 then P limbs
+    const int e = chunk * kThreads + threadIdx.x;
+    if (e >= A.N) return;
+    const bool isq = x < A.level;
+    const int prime = isq ? x : A.L + (x - A.level);
+    const ModQ m = A.mods[prime];
+    const u64 q = m.q;
+    const int my_digit = isq ? x / A.alpha : -1;
+    Acc128 acc0, acc1;
+    acc0.zero();
+    acc1.zero();
+    const i64 key_row = (i64)prime * A.N + e;
+    for (int t = 2; t <= A.n; ++t) {
+        for (int beta = 0; beta < A.n_digits; ++beta) {
+            u64 term;
+            if (beta == my_digit)
+                term = A.d.ptr[(i64)b * A.d.bstride + (i64)t * A.d.pstride + (i64)x * A.N + e];
+            else
+                term = A.ext.ptr[(i64)b * A.ext.bstride + (i64)((t - 2) * A.n_digits + beta) * A.ext.pstride +
+                                 (i64)x * A.N + e];
+            const u64 *key = A.keys + ((i64)((t - 2) * A.key_digits + beta) * 2) * A.key_pstride;
+            acc0.mac(term, key[key_row], q);
+            acc1.mac(term, key[A.key_pstride + key_row], q);
+        }
+    }
+    u64 *dst = A.acc.ptr + (i64)b * A.acc.bstride + (i64)x * A.N + e;
+    dst[0] = redc(acc0.hi, acc0.lo, m);
+    dst[A.acc.pstride] = redc(acc1.hi, acc1.lo, m);
+}
+
+cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
+    const int chunks = (A.N + kThreads - 1) / kThreads;
+    long long blocks = (long long)chunks * (A.level + A.K) * A.n_batch;
+    count_kernel(C);
+    // per batch element: (n-1) * digits terms and 2 outputs per target limb;
+    // key limbs counted once per launch
+    const double terms = (double)(A.n - 1) * A.n_digits;
+    const double limbs = (double)(A.level + A.K);
+    double bytes = ((terms + 2.0) * A.n_batch + 2.0 * terms) * limbs * A.N * sizeof(u64);
+    ProfScope ps(C, KC_MAC, bytes, st);
+    mac_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Rescale chain among the mu top limbs (coefficient domain), in place:
+// a^{(t),{u}} = q_{l-u}^-1 (a^{(t),{u-1}} - a^{(l-u),{u-1}}) mod q_t for
+// u = 1..mu-1 and t < l-u (Eq. 6 applied inside Algorithm 1, step 2).
+// After it, limb t holds a^{(t),{l-1-t}}.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) rschain_kernel(RsChainArgs A) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 per = (i64)A.n_polys * A.N;
+    if (gid >= per * A.n_batch) return;
+    const int b = (int)(gid / per);
+    const int p = (int)((gid % per) / A.N);
+    const int e = (int)(gid % A.N);
+    u64 *base = A.v.ptr + (i64)b * A.v.bstride + (i64)p * A.v.pstride + e;  // slot 0 = limb level - mu
+    const int l0 = A.level - A.mu;
+    u64 a[CKKS_MAX_PRIMES];
+    for (int t = 0; t < A.mu; ++t) a[t] = base[(i64)t * A.N];
+    for (int u = 1; u < A.mu; ++u) {
+        const int top = A.mu - u;  // index of limb level-u
+        const int ptop = l0 + top;
+        for (int t = 0; t < top; ++t) {
+            const int pt = l0 + t;
+            const u64 qt = A.mods[pt].q;
+            const Shoup one = A.one[pt];
+            const u64 tr = shoup(a[top], one.w, one.wp, qt);  // a[top] mod q_t
+            const Shoup inv = A.invq[ptop * CKKS_MAX_PRIMES + pt];
+            a[t] = shoup(sub_mod(a[t], tr, qt), inv.w, inv.wp, qt);
+        }
+    }
+    for (int t = 0; t < A.mu - 1; ++t) base[(i64)t * A.N] = a[t];
+}
+
+cudaError_t launch_rschain(const Context &C, const RsChainArgs &A, cudaStream_t st) {
+    if (A.mu < 2) return cudaSuccess;
+    i64 total = (i64)A.n_batch * A.n_polys * A.N;
+    count_kernel(C);
+    ProfScope ps(C, KC_RSCHAIN, 2.0 * A.n_batch * A.n_polys * A.mu * A.N * sizeof(u64), st);
+    rschain_kernel<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// keys
+// ---------------------------------------------------------------------------
+// In place: v <- v * fold[x] R^-1, fold = P^-1 R^2 on Q limbs, R^2 on P
+// limbs, giving the Montgomery form of P^-1 ek (Q limbs) or ek (P limbs).
+__global__ void __launch_bounds__(kThreads) keyprep_kernel(u64 *keys, i64 n_rows, int n_primes, int N,
+                                                           const ModQ *mods, const u64 *fold) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n_rows * N) return;
+    const int x = (int)((gid / N) % n_primes);
+    keys[gid] = mont_mul(keys[gid], fold[x], mods[x]);
+}
+
+cudaError_t launch_keyprep(const Context &C, u64 *keys, long long n_rows, cudaStream_t st) {
+    i64 total = n_rows * C.N;
+    count_kernel(C);
+    keyprep_kernel<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        keys, n_rows, C.L + C.K, C.N, C.d_mods, C.d_keyfold);
+    return cudaGetLastError();
+}
+
+// Small signed coefficients -> residues for every prime: out[x][i] = v[i] mod prime_x.
+__global__ void __launch_bounds__(kThreads) signed_to_res_kernel(const i64 *v, u64 *out, int n_primes, int N,
+                                                                 const ModQ *mods) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (i64)n_primes * N) return;
+    const int x = (int)(gid / N);
+    const int i = (int)(gid % N);
+    const i64 s = v[i];
+    const u64 q = mods[x].q;
+    out[gid] = s >= 0 ? ((u64)s) % q : q - (((u64)(-s)) % q);
+}
+
+cudaError_t launch_signed_to_res(const Context &C, const long long *v, u64 *out, cudaStream_t st) {
+    i64 total = (i64)(C.L + C.K) * C.N;
+    count_kernel(C);
+    signed_to_res_kernel<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        (const i64 *)v, out, C.L + C.K, C.N, C.d_mods);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ u64 mulmod_full(u64 a, u64 b, ModQ m, u64 r2) {
+    return mont_mul(mont_mul(a, b, m), r2, m);
+}
+
+// St <- St * S (pointwise, every prime)
+__global__ void __launch_bounds__(kThreads) pointwise_mul_kernel(u64 *St, const u64 *S, int n_primes, int N,
+                                                                 const ModQ *mods, const u64 *r2) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (i64)n_primes * N) return;
+    const int x = (int)(gid / N);
+    St[gid] = mulmod_full(St[gid], S[gid], mods[x], r2[x]);
+}
+
+cudaError_t launch_pointwise_mul(const Context &C, u64 *St, const u64 *S, cudaStream_t st) {
+    i64 total = (i64)(C.L + C.K) * C.N;
+    count_kernel(C);
+    pointwise_mul_kernel<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        St, S, C.L + C.K, C.N, C.d_mods, C.d_r2);
+    return cudaGetLastError();
+}
+
+// ek0 = E - a S + [P G_beta]_x S^t,  ek1 = a   (all L + K limbs, NTT domain)
+__global__ void __launch_bounds__(kThreads) keygen_kernel(const u64 *S, const u64 *St, const u64 *E, const u64 *a,
+                                                          u64 *ek, int n_primes, int N, const ModQ *mods,
+                                                          const u64 *r2, const Shoup *pg) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 plane = (i64)n_primes * N;
+    if (gid >= plane) return;
+    const int x = (int)(gid / N);
+    const ModQ m = mods[x];
+    const u64 q = m.q;
+    u64 as = mulmod_full(a[gid], S[gid], m, r2[x]);
+    u64 v = sub_mod(E[gid], as, q);
+    const Shoup c = pg[x];
+    v = add_mod(v, shoup(St[gid], c.w, c.wp, q), q);
+    ek[gid] = v;
+    ek[plane + gid] = a[gid];
+}
+
+cudaError_t launch_keygen(const Context &C, const u64 *S, const u64 *St, const u64 *E, const u64 *a, u64 *ek,
+                          int beta, cudaStream_t st) {
+    i64 total = (i64)(C.L + C.K) * C.N;
+    count_kernel(C);
+    keygen_kernel<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        S, St, E, a, ek, C.L + C.K, C.N, C.d_mods, C.d_r2, C.d_pgadget + (i64)beta * (C.L + C.K));
+    return cudaGetLastError();
+}
+
+}  // namespace ckks

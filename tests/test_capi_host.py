@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/ckks_mulk.h declares, and its planner (host C++)
+agrees with the partition rules of Section V-C and Table II."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import plan as oplan
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2601_15401_gb300 import build as B
+    B.build()
+    from paper_2601_15401_gb300._lib import lib
+    return lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ckks_mulk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(ckks_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    from paper_2601_15401_gb300._lib import SIGNATURES
+    assert set(names) == set(SIGNATURES)
+
+
+def test_strerror(L):
+    assert L.ckks_strerror(0) == b"ok"
+    assert L.ckks_strerror(-4) == b"workspace too small"
+
+
+def _describe(L, k, part):
+    h = ctypes.c_void_p()
+    rc = L.ckks_plan_create(None, k, part.encode() if part else None, ctypes.byref(h))
+    if rc != 0:
+        return rc, None
+    d, r, n = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    assert L.ckks_plan_describe(h, ctypes.byref(d), ctypes.byref(r), ctypes.byref(n)) == 0
+    L.ckks_plan_destroy(h)
+    return 0, (d.value, r.value, n.value)
+
+
+@pytest.mark.parametrize("k", range(2, 13))
+def test_default_plans_match_table_ii(L, k):
+    rc, (depth, rs, nodes) = _describe(L, k, None)
+    assert rc == 0
+    root = oplan.parse(oplan.TABLE_II[k], k)
+    assert depth == root.depth() == (k - 1).bit_length()
+    assert rs == oplan.rs_units(root)
+
+
+def test_plan_rejections(L):
+    assert _describe(L, 6, "(5,1)|(3,2)")[0] == -1      # depth rule (Section V-C)
+    assert _describe(L, 6, "(2,2,2)")[0] == 0
+    assert _describe(L, 4, "(1,1,1,1)")[0] == -1        # depth 3 > 2
+    assert _describe(L, 5, "(2,2)")[0] == -1            # sizes do not add up
+    assert _describe(L, 7, "(4,3)|(2,1)")[0] == -1      # no group of 3 split (2,1)? it is valid
