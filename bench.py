@@ -1,0 +1,490 @@
+#!/usr/bin/env python3
+"""Throughput of k-input RNS-CKKS ciphertext multiplication on GB300.
+
+Workload (one "step"): for every k in 4..12, one batched k-input multiply of
+16 independent products with Table II's partition, N = 2^16, 24 x 50-bit Q
+primes, 8 x 60-bit P primes, dnum = 3, input level 24, evaluation keys
+ek_2..ek_12 resident in HBM. 144 products per step. Inputs are uniform
+residues (the distribution of RLWE ciphertexts) drawn on the device with a
+seeded generator; they total ~27 GB, far above the 129 MB L2, so no L2 flush
+is needed between steps.
+
+Printed JSON line: value = products per second over the whole step (all N
+ranks), e2e = the same with host buffers (pinned host -> device copies of the
+step's inputs and device -> host copies of its outputs inside the timed
+region), roofline of the dominant kernel class (CUDA-event timed inside the
+timed region), per-k comparisons against chained standard 2-input
+multiplies (Table VII's binary tree) and one product per launch, and the CPU
+oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle (the only reference: the paper has no
+code) on the same workload, one full-size k = 4 product per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "k-input ct-mults/s at N=2^16 (k=4..12, batch 16 per k)"
+UNIT = "ct-mults/s"
+KS = list(range(4, 13))
+BATCH = 16
+CONFIG = {
+    "workload": "k-input CKKS multiply, N=2^16, L=24x50-bit q + K=8x60-bit p, dnum=3, level 24, "
+                "k=4..12 (Table II partitions), batch 16 per k",
+    "N": 65536, "L": 24, "K": 8, "dnum": 3, "level": 24, "ks": KS, "batch_per_k": BATCH,
+    "products_per_step": BATCH * len(KS),
+    "l2": "inputs (~27 GB) larger than L2; no flush",
+}
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def binary_tree(k):
+    if k == 1:
+        return None
+    a = 1 << (k - 1).bit_length() - 1
+    if k == 2:
+        return (1, 1)
+    return (a, k - a)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2601_15401_gb300 as G
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    params = synth.params_large()
+    N, L, K = params.N, params.L, params.K
+    ks = [int(x) for x in args.ks.split(",")] if args.ks else KS
+    B = args.batch
+    t_max = max(ks)
+    ctx = G.Context.from_params(params, device=local_rank)
+
+    # evaluation keys ek_2..ek_tmax, generated on the device from seeded draws
+    g = synth.rng(3, 0, stream=1)
+    s = torch.from_numpy(synth.ternary_secret(g, N)).to(dev)
+    e = torch.from_numpy(__import__("numpy").stack(
+        [[synth.gaussian(g, N) for _ in range(params.dnum)] for _ in range(t_max - 1)])).to(dev)
+    a = synth.uniform_residues_torch(list(params.q) + list(params.p), (t_max - 1, params.dnum), N, 0x51, dev)
+    keys = torch.empty((t_max - 1, params.dnum, 2, L + K, N), dtype=torch.uint64, device=dev)
+    kws = torch.empty(ctx.keygen_workspace_size() // 8, dtype=torch.uint64, device=dev)
+    ctx.keygen_evk(t_max, s, a, e, keys, kws)
+    del a, kws
+    evk = ctx.evk_set(t_max, keys)
+
+    # inputs / outputs per k (batched tensors [B][k][2][L][N])
+    inp, outs, tup, otup, depth = {}, {}, {}, {}, {}
+    ws_bytes = 0
+    for k in ks:
+        d = ctx.plan_describe(k)["depth"]
+        depth[k] = d
+        inp[k] = synth.uniform_residues_torch(params.q, (B, k, 2), N, 1000 + k + 97 * rank, dev)
+        outs[k] = torch.empty((B, 2, L - d, N), dtype=torch.uint64, device=dev)
+        tup[k] = [[G.Tuple(inp[k][b, u], 2, L, L, 1, 2.0 ** 50) for u in range(k)] for b in range(B)]
+        otup[k] = [G.Tuple(outs[k][b], 2, L - d, L - d) for b in range(B)]
+        ws_bytes = max(ws_bytes, ctx.workspace_size(k, L, B))
+    ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.uint64, device=dev)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    lat = {k: [] for k in ks}
+
+    def step(record=False):
+        evs = []
+        for k in ks:
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            ctx.mul_k_batch(tup[k], evk, otup[k], ws, stream=stream)
+            if record:
+                e1.record(stream)
+                evs.append((k, e0, e1))
+        return evs
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    ctx.counters(reset=True)
+    ctx.profile(True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    all_evs = []
+    t0.record(stream)
+    for _ in range(args.steps):
+        all_evs += step(record=True)
+    t1.record(stream)
+    t1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ctx.profile(False)
+    ms_total = t0.elapsed_time(t1)
+    prof = ctx.profile_read()
+    launches = ctx.counters()["kernels"]
+    ctx.check()
+    for k, e0, e1 in all_evs:
+        lat[k].append(e0.elapsed_time(e1))
+    ms_step = ms_total / args.steps
+    if world > 1:
+        tt = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    products = B * len(ks) * world
+    value = products / (ms_step / 1e3)
+
+    # dominant kernel class and its roofline
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"]) if prof else (None, None)
+    roofline = None
+    if dom[0]:
+        st = dom[1]
+        achieved = st["alg_bytes"] / (st["total_ms"] / 1e3) / 1e9
+        traffic = None
+        try:
+            ts = json.load(open(PROFILE_SUMMARY))
+            ent = ts.get("kernels", {}).get(dom[0])
+            if ent and ent.get("source_hash") == source_hash():
+                traffic = ent.get("dram_bytes_per_launch")
+        except Exception:
+            pass
+        roofline = {"bound": "hbm", "kernel": dom[0], "achieved": round(achieved, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+                    "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
+                    "avg_launch_us": st["total_ms"] * 1e3 / st["launches"]}
+    kernel_table = {n: {"launches": v["launches"] // args.steps, "ms_per_step": round(v["total_ms"] / args.steps, 3),
+                        "share": round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4),
+                        "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)}
+                    for n, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])}
+    # whole-step algorithmic bytes: inputs + outputs + keys once per step
+    in_bytes = sum(B * k * 2 * L * N * 8 for k in ks)
+    out_bytes = sum(B * 2 * (L - depth[k]) * N * 8 for k in ks)
+    lat_all = [x for k in ks for x in lat[k]]
+    per_k = {}
+    for k in ks:
+        xs = sorted(lat[k])
+        per_k[k] = {"batch_ms_p50": round(statistics.median(xs), 3), "kinput_ctmults_s": round(B / (statistics.median(xs) / 1e3), 1)}
+
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded uniform residues, seeded key draws)",
+        "config": dict(CONFIG, ks=ks, batch_per_k=B, products_per_step=B * len(ks),
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "gpu_launches": int(launches),
+        "latency_ms": {"per_batch_p50": round(statistics.median(lat_all), 3),
+                       "per_batch_p99": round(sorted(lat_all)[max(0, math.ceil(0.99 * len(lat_all)) - 1)], 3)},
+        "roofline": roofline,
+        "kernels": kernel_table,
+        "step_alg_GBps": round((in_bytes + out_bytes) / (ms_step / 1e3) / 1e9, 1),
+        "per_k": per_k,
+        "clocks": clk,
+    }
+
+    # ---------------- comparators (outside the timed region)
+    if not args.no_compare and rank == 0:
+        reps = 2
+        torch.cuda.synchronize()
+        for k in ks:
+            # one product per launch
+            ws1 = torch.empty(ctx.workspace_size(k, L, 1) // 8 + 1, dtype=torch.uint64, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for r in range(reps + 1):
+                if r == 1:
+                    e0.record(stream)
+                for b in range(B):
+                    ctx.mul_k(tup[k][b], evk, otup[k][b], ws1, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            per_k[k]["one_per_launch_ctmults_s"] = round(B * reps / (e0.elapsed_time(e1) / 1e3), 1)
+            del ws1
+            # chained standard 2-input multiplies along the binary tree (batched over B)
+            ms = chained_ms(ctx, evk, inp[k], k, B, L, N, dev, stream, reps)
+            per_k[k]["chained_2input_ctmults_s"] = round(B / (ms / 1e3), 1)
+            per_k[k]["speedup_vs_chained"] = round(per_k[k]["kinput_ctmults_s"] / per_k[k]["chained_2input_ctmults_s"], 3)
+            per_k[k]["speedup_vs_one_per_launch"] = round(per_k[k]["kinput_ctmults_s"] / per_k[k]["one_per_launch_ctmults_s"], 3)
+        ctx.check()
+
+    # ---------------- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        result["e2e"] = e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, inp[max(ks)])
+
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_baseline(args)
+    return result
+
+
+def chained_ms(ctx, evk, inp, k, B, L, N, dev, stream, reps):
+    """Time the binary tree of standard 2-input multiplies over the batch."""
+    import torch
+
+    import paper_2601_15401_gb300 as G
+    bufs = []
+    ws = torch.empty(ctx.mul2_workspace_size(L, B) // 8 + 1, dtype=torch.uint64, device=dev)
+
+    def mul2(x, y):
+        (tx, lx), (ty, ly) = x, y
+        lv = min(lx, ly)
+        o = torch.empty((B, 2, lv - 1, N), dtype=torch.uint64, device=dev)
+        bufs.append(o)
+        a = [G.Tuple(tx[b], 2, lv, tx.shape[2]) for b in range(B)]
+        c = [G.Tuple(ty[b], 2, lv, ty.shape[2]) for b in range(B)]
+        oo = [G.Tuple(o[b], 2, lv - 1, lv - 1) for b in range(B)]
+        ctx.mul2_batch(a, c, evk, oo, ws, stream=stream)
+        return (o, lv - 1)
+
+    def tree(lo, n):
+        if n == 1:
+            return (inp[:, lo], L)
+        a = 1 << (n - 1).bit_length() - 1
+        if n == 2:
+            a = 1
+        return mul2(tree(lo, a), tree(lo + a, n - a))
+
+    tree(0, k)  # warm-up
+    torch.cuda.synchronize()
+    bufs.clear()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        tree(0, k)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, src):
+    """Same step through the C ABI, with the inputs copied from pinned host
+    memory and the outputs copied back to it inside the timed region."""
+    import torch
+
+    import paper_2601_15401_gb300 as G
+    kmax = max(ks)
+    host_in = torch.empty((B, kmax, 2, L, N), dtype=torch.uint64, pin_memory=True)
+    host_in.copy_(src)  # the step's synthetic inputs, staged in pinned host memory
+    host_out = {k: torch.empty((B, 2, L - depth[k], N), dtype=torch.uint64, pin_memory=True) for k in ks}
+    dev_in = torch.empty((B, kmax, 2, L, N), dtype=torch.uint64, device=dev)
+    dev_out = {k: torch.empty((B, 2, L - depth[k], N), dtype=torch.uint64, device=dev) for k in ks}
+    tup = {k: [[G.Tuple(dev_in[b, u], 2, L, L) for u in range(k)] for b in range(B)] for k in ks}
+    otup = {k: [G.Tuple(dev_out[k][b], 2, L - depth[k], L - depth[k]) for b in range(B)] for k in ks}
+    h2d = sum(B * k * 2 * L * N * 8 for k in ks)
+    d2h = sum(B * 2 * (L - depth[k]) * N * 8 for k in ks)
+
+    def step():
+        for k in ks:
+            for b in range(B):
+                dev_in[b, :k].copy_(host_in[b, :k], non_blocking=True)
+            ctx.mul_k_batch(tup[k], evk, otup[k], ws, stream=stream)
+            host_out[k].copy_(dev_out[k], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    ctx.check()
+    return {"value": round(B * len(ks) * world / (ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_setup(k):
+    import synth
+    from oracle import ckks as O
+    params = synth.params_large()
+    octx = O.Ctx(params)
+    km = synth.key_material(params, k, 3)
+    keys = O.keygen_all(octx, km, k)
+    cts = [O.Tup(synth.uniform_tuple(params, 2, params.L, 3, i), 2.0 ** 50) for i in range(k)]
+    return octx, keys, cts
+
+
+def oracle_product_seconds(octx, keys, cts) -> float:
+    from oracle import ckks as O
+    t = time.time()
+    O.mul_k(octx, cts, keys)
+    return time.time() - t
+
+
+def cpu_baseline(args):
+    from oracle import ring
+    k = 4
+    octx, keys, cts = _oracle_setup(k)
+    sec = oracle_product_seconds(octx, keys, cts)
+    return {"value": round(1.0 / sec, 4), "unit": UNIT, "cores": ring.num_threads(), "kind": "oracle",
+            "sample": f"one full-size k={k} product (N=2^16, L=24, K=8, dnum=3) of the step's 144; "
+                      f"{sec:.1f} s; k=4 is the cheapest k of the step, so the mix runs slower"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from oracle import ring
+    k = 4
+    octx, keys, cts = _oracle_setup(k)
+    for _ in range(min(args.warmup, 1)):
+        oracle_product_seconds(octx, keys, cts)
+    times = []
+    budget = 200.0
+    t_start = time.time()
+    for i in range(args.steps):
+        times.append(oracle_product_seconds(octx, keys, cts))
+        if time.time() - t_start > budget:
+            break
+    sec = statistics.mean(times)
+    v = round(1.0 / sec, 4)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": round(sec * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded uniform residues, seeded key draws)",
+            "config": dict(CONFIG, reference_step="one full-size k=4 product (the cheapest k of the step)"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": ring.num_threads(),
+                             "sample": "one full-size k=4 product per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2601_15401_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--ks", default="")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

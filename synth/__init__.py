@@ -218,3 +218,18 @@ def public_key_draw(params: Params, config: int):
     """(a, e) for the public key: a uniform on every Q limb (NTT domain)."""
     g = rng(config, 0, stream=4)
     return uniform_residues(g, params.q, params.N), gaussian(g, params.N)
+
+
+# ----------------------------------------------------------------------------
+# device-side draws for large throughput runs (same distributions)
+# ----------------------------------------------------------------------------
+def uniform_residues_torch(primes, shape_prefix, N: int, seed: int, device):
+    """Tensor [*shape_prefix][len(primes)][N] of uniform residues, limb j in
+    [0, primes[j]), drawn on `device` with a seeded torch generator."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed & 0x7FFFFFFFFFFFFFFF)
+    out = torch.empty((*shape_prefix, len(primes), N), dtype=torch.int64, device=device)
+    for j, q in enumerate(primes):
+        out[..., j, :] = torch.randint(0, int(q), (*shape_prefix, N), generator=g, dtype=torch.int64, device=device)
+    return out.view(torch.uint64)
