@@ -10,7 +10,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libckks_mulk.so")
+LIB = os.environ.get("CKKS_MULK_LIB", os.path.join(HERE, "libckks_mulk.so"))
 SOURCES = ["ntt.cu", "rns.cu", "context.cu", "engine.cu", "capi.cu", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -24,7 +24,8 @@ def nvcc() -> str:
 
 
 def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    tag = os.path.basename(LIB).replace(".so", "")
+    obj = os.path.join(BUILD, f"{tag}_{os.path.basename(src)}.o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-I", os.path.join(HERE, "..", "include"), "-c",
            os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
@@ -48,7 +49,7 @@ def build(force: bool = False, extra: list[str] | None = None, verbose: bool = F
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra or [])
+    extra = list(extra or []) + os.environ.get("CKKS_NVCC_FLAGS", "").split()
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"

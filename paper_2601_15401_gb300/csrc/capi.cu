@@ -405,7 +405,10 @@ int ckks_rescale_multi(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckk
 static int transform_api(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *stream, bool fwd) {
     if (!ctx || !in || !out || !out->data) return CKKS_EINVAL;
     const Context &C = ctx->c;
-    if (!tuple_ok(in, C.L)) return CKKS_EINVAL;
+    // plain transforms take any number of polynomials
+    if (!in->data || in->level < 1 || in->level > (uint32_t)C.L || in->poly_stride < in->level || in->n_polys < 1 ||
+        in->n_polys > 65535)
+        return CKKS_EINVAL;
     if (out->poly_stride == 0) out->poly_stride = in->poly_stride;
     if (out->poly_stride < in->level) return CKKS_EINVAL;
     cudaSetDevice(C.device);

@@ -81,6 +81,20 @@ struct Acc128 {
     }
 };
 
+// Same accumulation without the per-term reduction: valid when the sum of
+// the left operands' moduli is below 2^64 (checked at context creation for
+// every BConv digit and for the P basis), which keeps hi < q.
+struct Acc128Lazy {
+    u64 hi, lo;
+    __device__ __forceinline__ void zero() { hi = 0; lo = 0; }
+    __device__ __forceinline__ void mac(u64 a, u64 b) {
+        u64 plo = a * b;
+        u64 phi = mulhi64(a, b);
+        lo += plo;
+        hi += phi + (lo < plo ? 1ull : 0ull);
+    }
+};
+
 // Shoup constant pair.
 struct Shoup {
     u64 w, wp;

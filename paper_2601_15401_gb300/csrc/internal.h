@@ -34,7 +34,7 @@ enum OpCounter {
 
 struct NttPhase {
     int N, N1, N2;
-    int sub_per_tile;
+    int sub_per_tile, log_sub, log_n2;
     const ModQ *mods;
     const ulonglong2 *tw_fwd;
     const ulonglong2 *tw_inv;

@@ -66,43 +66,174 @@ struct Pass {
     static constexpr int start = P * base + (P < extra ? P : extra);
 };
 
-// Shared-memory layouts of a tile.
-//   columns: [n][C] row-major (C sub-problems side by side); thread index
-//            runs over sub-problems fastest.
-//   blocks:  [B][n + n/16] with one pad word per 16; thread index runs over
+// Shared-memory layouts of a tile (n_sub = 2^lsub sub-problems of n points).
+//   columns: [n][n_sub] row-major (sub-problems side by side); threads run
+//            over sub-problems fastest, so every pass reads whole 128-byte
+//            row segments of global memory.
+//   blocks:  [n_sub][n + n/16] with one pad word per 16; threads run over
 //            point sets fastest.
-template <bool COLS>
+template <bool COLS, int LOGN>
 struct Layout {
-    int n_sub, n;
+    int lsub;
     __device__ __forceinline__ int off(int sp, int k) const {
-        if (COLS) return k * n_sub + sp;
-        return sp * (n + (n >> 4)) + k + (k >> 4);
+        if (COLS) return (k << lsub) + sp;
+        return sp * ((1 << LOGN) + (1 << LOGN >> 4)) + k + (k >> 4);
     }
-    __device__ __forceinline__ void split(int s, int sets, int &sp, int &set) const {
-        if (COLS) { sp = s % n_sub; set = s / n_sub; }
-        else { set = s % sets; sp = s / sets; }
+    __device__ __forceinline__ void split(int s, int lsets, int &sp, int &set) const {
+        if (COLS) { sp = s & ((1 << lsub) - 1); set = s >> lsub; }
+        else { set = s & ((1 << lsets) - 1); sp = s >> lsets; }
     }
 };
 
-template <int LOGN, int R, int E0, bool FWD, bool COLS>
-__device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS> &lay, const ulonglong2 *tw,
-                                         int tw_b0, int tw_bmul, u64 q) {
+// ---------------------------------------------------------------------------
+// fused element-wise load / store with per-CTA base pointers
+// ---------------------------------------------------------------------------
+struct LoadCtx {
+    int mode;
+    const u64 *a, *b;      // limb base pointers (b: T limbs / z limbs / second addend)
+    const Shoup *g;        // LD_EQ17: g[0..mu-1], g[mu] = self
+    int mu, with_self, K, N;
+    const u64 *cK;         // LD_BCONVK
+    ModQ m;
+};
+
+struct StoreCtx {
+    int mode;
+    u64 *dst;
+    const u64 *aux, *aux2;
+    Shoup c;
+    int K, N;
+    const u64 *cK;
+    ModQ m;
+};
+
+__device__ __forceinline__ LoadCtx make_load(const LoadSpec &L, const LimbJobs &J, int N, int b, int p, int l,
+                                             int prime, ModQ m) {
+    LoadCtx c;
+    c.mode = L.mode;
+    c.N = N;
+    c.m = m;
+    c.mu = L.mu;
+    c.with_self = L.with_self;
+    c.K = L.K;
+    const int slot = J.slot[l];
+    c.a = L.a.ptr ? limb_ptr(L.a, b, p, slot, N) : nullptr;
+    c.b = nullptr;
+    c.g = nullptr;
+    c.cK = nullptr;
+    if (L.mode == LD_ADD) c.b = limb_ptr(L.b, b, p, slot, N);
+    if (L.mode == LD_EQ17 || L.mode == LD_BCONVK) c.b = L.b.ptr + (i64)b * L.b.bstride + (i64)p * L.b.pstride;
+    if (L.mode == LD_EQ17) c.g = L.g + (i64)l * (L.mu + 1);
+    if (L.mode == LD_BCONVK) c.cK = L.cK + (i64)prime * CKKS_MAX_PRIMES;
+    return c;
+}
+
+__device__ __forceinline__ StoreCtx make_store(const StoreSpec &S, const LimbJobs &J, int N, int b, int p, int l,
+                                               int prime, ModQ m) {
+    StoreCtx c;
+    c.mode = S.mode;
+    c.N = N;
+    c.m = m;
+    c.K = S.K;
+    const int ds = J.dslot[l];
+    c.dst = limb_ptr(S.dst, b, p, ds, N);
+    c.aux = nullptr;
+    c.aux2 = nullptr;
+    c.cK = nullptr;
+    c.c = Shoup{0, 0};
+    if (S.mode == ST_SCALE || S.mode == ST_MODDOWN || S.mode == ST_MRS) c.c = S.c[l * S.c_stride];
+    if (S.mode == ST_MODDOWN) {
+        c.aux = S.aux.ptr + (i64)b * S.aux.bstride + (i64)p * S.aux.pstride;
+        c.cK = S.cK + (i64)prime * CKKS_MAX_PRIMES;
+    }
+    if (S.mode == ST_MRS || S.mode == ST_ADDSUB) c.aux = limb_ptr(S.aux, b, p, ds, N);
+    if (S.mode == ST_ADDSUB) c.aux2 = limb_ptr(S.aux2, b, p, ds, N);
+    return c;
+}
+
+__device__ __forceinline__ u64 load_elem(const LoadCtx &c, int e) {
+    const u64 q = c.m.q;
+    switch (c.mode) {
+    case LD_ADD:
+        return add_mod(c.a[e], c.b[e], q);
+    case LD_EQ17: {
+        // sum_t g_t T_t (mod q); with the self term: g_self a - sum
+        u64 s = 0;
+        for (int t = 0; t < c.mu; ++t) s = add_mod(s, shoup(c.b[(i64)t * c.N + e], c.g[t].w, c.g[t].wp, q), q);
+        if (c.with_self) s = sub_mod(shoup(c.a[e], c.g[c.mu].w, c.g[c.mu].wp, q), s, q);
+        return s;
+    }
+    case LD_BCONVK: {
+        Acc128Lazy acc;  // sum of the P primes < 2^64 (context check)
+        acc.zero();
+        for (int i = 0; i < c.K; ++i) acc.mac(c.b[(i64)i * c.N + e], c.cK[i]);
+        return redc(acc.hi, acc.lo, c.m);
+    }
+    default:
+        return c.a[e];
+    }
+}
+
+__device__ __forceinline__ void store_elem(const StoreCtx &c, int e, u64 v, bool fwd) {
+    const u64 q = c.m.q;
+    switch (c.mode) {
+    case ST_LAZY:
+        c.dst[e] = v;
+        break;
+    case ST_SCALE:
+        c.dst[e] = shoup(v, c.c.w, c.c.wp, q);
+        break;
+    case ST_MODDOWN: {
+        // c* = v N^-1 - sum_i z_i [p_i^-1 R]_q  (Eq. 5 with Eq. 11 / 12)
+        u64 x = shoup(v, c.c.w, c.c.wp, q);
+        Acc128Lazy acc;  // sum of the P primes < 2^64 (context check)
+        acc.zero();
+        for (int i = 0; i < c.K; ++i) acc.mac(c.aux[(i64)i * c.N + e], c.cK[i]);
+        c.dst[e] = sub_mod(x, redc(acc.hi, acc.lo, c.m), q);
+        break;
+    }
+    case ST_MRS:
+        // Algorithm 1, last step: A' = g^{mu,L-1} A - B
+        c.dst[e] = sub_mod(shoup(c.aux[e], c.c.w, c.c.wp, q), fwd ? reduce4(v, q) : reduce2(v, q), q);
+        break;
+    case ST_ADDSUB:
+        c.dst[e] = sub_mod(add_mod(c.aux[e], c.aux2[e], q), fwd ? reduce4(v, q) : reduce2(v, q), q);
+        break;
+    default:  // ST_REDUCE
+        c.dst[e] = fwd ? reduce4(v, q) : reduce2(v, q);
+        break;
+    }
+}
+
+// One pass of R stages starting at local stage E0 on every point set of the
+// tile. SRC/DST: 0 = shared memory, 1 = global (fused load / store).
+template <int LOGN, int R, int E0, bool FWD, bool COLS, bool GIN, bool GOUT>
+__device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay, const ulonglong2 *tw, int tw_b0,
+                                         int tw_bmul, u64 q, const LoadCtx &lc, const StoreCtx &sc, int t0,
+                                         int log_n2) {
     constexpr int n = 1 << LOGN;
     constexpr int EL = 1 << R;
     constexpr int t_min = n >> (E0 + R);
-    constexpr int t0 = n >> (E0 + 1);
-    constexpr int sets = n >> R;
-    const int total = lay.n_sub * sets;
+    constexpr int t0s = n >> (E0 + 1);
+    constexpr int lsets = LOGN - R;
+    const int total = 1 << (lay.lsub + lsets);
     for (int s = threadIdx.x; s < total; s += blockDim.x) {
         int sp, set;
-        lay.split(s, sets, sp, set);
-        const int o = set % t_min;
+        lay.split(s, lsets, sp, set);
+        const int o = set & (t_min - 1);
         const int g = set / t_min;
-        const int base = g * 2 * t0 + o;
+        const int base = g * 2 * t0s + o;
         u64 x[EL];
 #pragma unroll
-        for (int k = 0; k < EL; ++k) x[k] = sm[lay.off(sp, base + k * t_min)];
-        // twiddle index m_loc * twb + i_loc with twb = tw_b0 + tw_bmul * sp
+        for (int k = 0; k < EL; ++k) {
+            const int pt = base + k * t_min;
+            if (GIN) {
+                const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
+                x[k] = load_elem(lc, e);
+            } else {
+                x[k] = sm[lay.off(sp, pt)];
+            }
+        }
         const int twb = tw_b0 + tw_bmul * sp;
         if (FWD) {
 #pragma unroll
@@ -132,101 +263,40 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS> &lay, const
             }
         }
 #pragma unroll
-        for (int k = 0; k < EL; ++k) sm[lay.off(sp, base + k * t_min)] = x[k];
-    }
-}
-
-template <int LOGN, bool FWD, bool COLS, int P>
-__device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS> &lay, const ulonglong2 *tw,
-                                           int tw_b0, int tw_bmul, u64 q) {
-    constexpr int NP = Pass<LOGN, 0>::NP;
-    if constexpr (P < NP) {
-        constexpr int PP = FWD ? P : NP - 1 - P;
-        run_pass<LOGN, Pass<LOGN, PP>::len, Pass<LOGN, PP>::start, FWD, COLS>(sm, lay, tw, tw_b0, tw_bmul, q);
-        __syncthreads();
-        run_passes<LOGN, FWD, COLS, P + 1>(sm, lay, tw, tw_b0, tw_bmul, q);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// fused element-wise load / store
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ u64 load_elem(const LoadSpec &L, const LimbJobs &J, int N, int b, int p, int l,
-                                         int prime, u64 q, int e) {
-    const int slot = J.slot[l];
-    switch (L.mode) {
-    case LD_ADD: {
-        u64 x = limb_ptr(L.a, b, p, slot, N)[e];
-        u64 y = limb_ptr(L.b, b, p, slot, N)[e];
-        return add_mod(x, y, q);
-    }
-    case LD_EQ17: {
-        // sum_t g_t T_t (mod q); with the self term: g_self a - sum
-        const Shoup *g = L.g + (i64)l * (L.mu + 1);
-        const u64 *T = L.b.ptr + (i64)b * L.b.bstride + (i64)p * L.b.pstride + e;
-        u64 s = 0;
-        for (int t = 0; t < L.mu; ++t) s = add_mod(s, shoup(T[(i64)t * N], g[t].w, g[t].wp, q), q);
-        if (L.with_self) {
-            u64 a = limb_ptr(L.a, b, p, slot, N)[e];
-            s = sub_mod(shoup(a, g[L.mu].w, g[L.mu].wp, q), s, q);
+        for (int k = 0; k < EL; ++k) {
+            const int pt = base + k * t_min;
+            if (GOUT) {
+                const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
+                store_elem(sc, e, x[k], FWD);
+            } else {
+                sm[lay.off(sp, pt)] = x[k];
+            }
         }
-        return s;
-    }
-    case LD_BCONVK: {
-        ModQ m = L.mods[prime];
-        const u64 *cK = L.cK + (i64)prime * CKKS_MAX_PRIMES;
-        const u64 *z = L.b.ptr + (i64)b * L.b.bstride + (i64)p * L.b.pstride + e;
-        Acc128 acc;
-        acc.zero();
-        for (int i = 0; i < L.K; ++i) acc.mac(z[(i64)i * N], cK[i], q);
-        return redc(acc.hi, acc.lo, m);
-    }
-    default:
-        return limb_ptr(L.a, b, p, slot, N)[e];
     }
 }
 
-__device__ __forceinline__ void store_elem(const StoreSpec &S, const LimbJobs &J, int N, int b, int p, int l,
-                                           int prime, u64 q, int e, u64 v, bool fwd) {
-    u64 *dst = limb_ptr(S.dst, b, p, J.dslot[l], N) + e;
-    switch (S.mode) {
-    case ST_LAZY:
-        *dst = v;
-        break;
-    case ST_SCALE: {
-        Shoup c = S.c[l * S.c_stride];
-        *dst = shoup(v, c.w, c.wp, q);
-        break;
-    }
-    case ST_MODDOWN: {
-        // c* = v N^-1 - sum_i z_i [p_i^-1 R]_q  (Eq. 5 with Eq. 11/12)
-        Shoup c = S.c[l * S.c_stride];
-        u64 x = shoup(v, c.w, c.wp, q);
-        ModQ m = S.mods[prime];
-        const u64 *cK = S.cK + (i64)prime * CKKS_MAX_PRIMES;
-        const u64 *z = S.aux.ptr + (i64)b * S.aux.bstride + (i64)p * S.aux.pstride + e;
-        Acc128 acc;
-        acc.zero();
-        for (int i = 0; i < S.K; ++i) acc.mac(z[(i64)i * N], cK[i], q);
-        *dst = sub_mod(x, redc(acc.hi, acc.lo, m), q);
-        break;
-    }
-    case ST_MRS: {
-        // Algorithm 1, last step: A' = g^{mu,L-1} A - B (A read from aux)
-        Shoup c = S.c[l * S.c_stride];
-        u64 a = limb_ptr(S.aux, b, p, J.dslot[l], N)[e];
-        *dst = sub_mod(shoup(a, c.w, c.wp, q), fwd ? reduce4(v, q) : reduce2(v, q), q);
-        break;
-    }
-    case ST_ADDSUB: {
-        u64 a = limb_ptr(S.aux, b, p, J.dslot[l], N)[e];
-        u64 c = limb_ptr(S.aux2, b, p, J.dslot[l], N)[e];
-        *dst = sub_mod(add_mod(a, c, q), fwd ? reduce4(v, q) : reduce2(v, q), q);
-        break;
-    }
-    default:  // ST_REDUCE
-        *dst = fwd ? reduce4(v, q) : reduce2(v, q);
-        break;
+// Direct global access is used on a side whose pass reads / writes at
+// least 8 consecutive words per sub-problem (always true for column tiles).
+template <int LOGN, bool COLS, int P>
+struct PassAccess {
+    static constexpr int t_min = (1 << LOGN) >> (Pass<LOGN, P>::start + Pass<LOGN, P>::len);
+    static constexpr bool direct = COLS || t_min >= 8;
+};
+
+template <int LOGN, bool FWD, bool COLS, int I>
+__device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS, LOGN> &lay, const ulonglong2 *tw, int tw_b0,
+                                           int tw_bmul, u64 q, const LoadCtx &lc, const StoreCtx &sc, int t0,
+                                           int log_n2) {
+    constexpr int NP = Pass<LOGN, 0>::NP;
+    if constexpr (I < NP) {
+        constexpr int PP = FWD ? I : NP - 1 - I;
+        constexpr bool first = I == 0, last = I == NP - 1;
+        constexpr bool gin = first && PassAccess<LOGN, COLS, PP>::direct;
+        constexpr bool gout = last && PassAccess<LOGN, COLS, PP>::direct;
+        run_pass<LOGN, Pass<LOGN, PP>::len, Pass<LOGN, PP>::start, FWD, COLS, gin, gout>(
+            sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
+        if (!last || !gout) __syncthreads();
+        run_passes<LOGN, FWD, COLS, I + 1>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
     }
 }
 
@@ -234,36 +304,52 @@ __device__ __forceinline__ void store_elem(const StoreSpec &S, const LimbJobs &J
 // the phase kernel
 // ---------------------------------------------------------------------------
 template <int LOGN, bool FWD, bool COLS>
-__global__ void __launch_bounds__(256) ntt_phase_kernel(NttPhase P, LimbJobs J, LoadSpec L, StoreSpec S) {
+#ifndef CKKS_NTT_MINB
+#define CKKS_NTT_MINB 2
+#endif
+__global__ void __launch_bounds__(256, CKKS_NTT_MINB) ntt_phase_kernel(NttPhase P, LimbJobs J, LoadSpec L, StoreSpec S) {
     extern __shared__ u64 sm[];
     constexpr int n = 1 << LOGN;
+    constexpr int NP = Pass<LOGN, 0>::NP;
     int b, p, l;
     decode_job(J, blockIdx.y, b, p, l);
     const int prime = J.prime[l];
-    const u64 q = P.mods[prime].q;
+    const ModQ m = P.mods[prime];
+    const u64 q = m.q;
     const ulonglong2 *tw = (FWD ? P.tw_fwd : P.tw_inv) + (i64)prime * P.N;
-    const int n_sub = P.sub_per_tile;
-    Layout<COLS> lay{n_sub, n};
-    const int t0 = blockIdx.x * n_sub;  // first column (COLS) or block (!COLS)
-    const int total = n_sub * n;
-    // global -> shared with the fused load
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int sp, k, e;
-        if (COLS) { k = idx / n_sub; sp = idx % n_sub; e = t0 + sp + k * P.N2; }
-        else { sp = idx / n; k = idx % n; e = (t0 + sp) * n + k; }
-        sm[lay.off(sp, k)] = load_elem(L, J, P.N, b, p, l, prime, q, e);
+    const int lsub = P.log_sub;
+    const int n_sub = 1 << lsub;
+    Layout<COLS, LOGN> lay{lsub};
+    const int t0 = blockIdx.x << lsub;  // first column (COLS) or block (!COLS)
+    const LoadCtx lc = make_load(L, J, P.N, b, p, l, prime, m);
+    const StoreCtx sc = make_store(S, J, P.N, b, p, l, prime, m);
+    constexpr int PF = FWD ? 0 : NP - 1;
+    constexpr int PL = FWD ? NP - 1 : 0;
+    constexpr bool gin = PassAccess<LOGN, COLS, PF>::direct;
+    constexpr bool gout = PassAccess<LOGN, COLS, PL>::direct;
+    const int total = n_sub << LOGN;
+    if (!gin) {
+        // coalesced global -> shared with the fused load
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int sp, k, e;
+            if (COLS) { k = idx >> lsub; sp = idx & (n_sub - 1); e = t0 + sp + (k << P.log_n2); }
+            else { sp = idx >> LOGN; k = idx & (n - 1); e = ((t0 + sp) << LOGN) + k; }
+            sm[lay.off(sp, k)] = load_elem(lc, e);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // twiddle base: columns -> 1; blocks -> N1 + block
     const int tw_b0 = COLS ? 1 : P.N1 + t0;
     const int tw_bmul = COLS ? 0 : 1;
-    run_passes<LOGN, FWD, COLS, 0>(sm, lay, tw, tw_b0, tw_bmul, q);
-    // shared -> global with the fused store
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int sp, k, e;
-        if (COLS) { k = idx / n_sub; sp = idx % n_sub; e = t0 + sp + k * P.N2; }
-        else { sp = idx / n; k = idx % n; e = (t0 + sp) * n + k; }
-        store_elem(S, J, P.N, b, p, l, prime, q, e, sm[lay.off(sp, k)], FWD);
+    run_passes<LOGN, FWD, COLS, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
+    if (!gout) {
+        // shared -> global with the fused store (coalesced)
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int sp, k, e;
+            if (COLS) { k = idx >> lsub; sp = idx & (n_sub - 1); e = t0 + sp + (k << P.log_n2); }
+            else { sp = idx >> LOGN; k = idx & (n - 1); e = ((t0 + sp) << LOGN) + k; }
+            store_elem(sc, e, sm[lay.off(sp, k)], FWD);
+        }
     }
 }
 
@@ -341,6 +427,9 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
         smem = (size_t)n_sub * (n + n / 16) * sizeof(u64);
     }
     P.sub_per_tile = n_sub;
+    P.log_sub = 0;
+    while ((1 << P.log_sub) < n_sub) ++P.log_sub;
+    P.log_n2 = log_n2;
     int per_sub = (1 << logn) >= 16 ? (1 << logn) / 16 : 1;  // radix-16 point sets per sub-problem
     int threads = ((n_sub * per_sub + 31) / 32) * 32;
     if (threads > 256) threads = 256;

@@ -13,6 +13,8 @@
 #include "internal.h"
 #include "rns.h"
 
+#include <algorithm>
+
 namespace ckks {
 
 static constexpr int kThreads = 256;
@@ -22,61 +24,70 @@ static constexpr int kThreads = 256;
 // wise in the NTT domain. Each child product is a Montgomery product, so the
 // result carries R^-(m-1); the final multiply by R^m (REDC) removes it.
 // ---------------------------------------------------------------------------
+// MAXT bounds every tuple size involved (children and output), so the
+// unrolled, predicated product loops stay short for small nodes.
+template <int MAXT>
 __global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
-    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    const i64 per_b = (i64)A.level * A.N;
-    if (gid >= per_b * A.n_batch) return;
-    const int b = (int)(gid / per_b);
-    const i64 r = gid % per_b;
-    const int j = (int)(r / A.N);
-    const int e = (int)(r % A.N);
+    const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;  // limb * N + coefficient
+    if (r >= (i64)A.level * A.N) return;
+    const int b = blockIdx.y;
+    const int j = (int)(r >> A.log_n);
     const ModQ m = A.mods[j];
     const u64 q = m.q;
-    u64 cur[CKKS_MAX_TUPLE];
+    u64 cur[MAXT];
     int ncur = A.child_polys[0];
     {
-        const u64 *src = A.child[0].ptr + (i64)b * A.child[0].bstride + (i64)j * A.N + e;
+        const u64 *src = A.child[0].ptr + (i64)b * A.child[0].bstride + r;
 #pragma unroll
-        for (int a = 0; a < CKKS_MAX_TUPLE; ++a)
-            cur[a] = a < ncur ? src[(i64)a * A.child[0].pstride] : 0ull;
+        for (int a = 0; a < MAXT; ++a) cur[a] = a < ncur ? src[(i64)a * A.child[0].pstride] : 0ull;
     }
     for (int c = 1; c < A.m; ++c) {
         const int ny = A.child_polys[c];
-        const u64 *src = A.child[c].ptr + (i64)b * A.child[c].bstride + (i64)j * A.N + e;
-        u64 y[CKKS_MAX_TUPLE];
+        const u64 *src = A.child[c].ptr + (i64)b * A.child[c].bstride + r;
+        u64 y[MAXT];
 #pragma unroll
-        for (int a = 0; a < CKKS_MAX_TUPLE; ++a) y[a] = a < ny ? src[(i64)a * A.child[c].pstride] : 0ull;
-        u64 nxt[CKKS_MAX_TUPLE];
+        for (int a = 0; a < MAXT; ++a) y[a] = a < ny ? src[(i64)a * A.child[c].pstride] : 0ull;
+        u64 nxt[MAXT];
 #pragma unroll
-        for (int t = 0; t < CKKS_MAX_TUPLE; ++t) {
+        for (int t = 0; t < MAXT; ++t) {
             Acc128 acc;
             acc.zero();
 #pragma unroll
             for (int a = 0; a <= t; ++a) {
                 if (a < ncur && t - a < ny) acc.mac(cur[a], y[t - a], q);
             }
-            nxt[t] = redc(acc.hi, acc.lo, m);
+            nxt[t] = t < ncur + ny - 1 ? redc(acc.hi, acc.lo, m) : 0ull;
         }
         ncur = ncur + ny - 1;
 #pragma unroll
-        for (int t = 0; t < CKKS_MAX_TUPLE; ++t) cur[t] = nxt[t];
+        for (int t = 0; t < MAXT; ++t) cur[t] = nxt[t];
     }
     const u64 fix = A.rpow[(i64)j * 16 + A.m];  // R^m
-    u64 *dst = A.out.ptr + (i64)b * A.out.bstride + (i64)j * A.N + e;
+    u64 *dst = A.out.ptr + (i64)b * A.out.bstride + r;
 #pragma unroll
-    for (int t = 0; t < CKKS_MAX_TUPLE; ++t)
+    for (int t = 0; t < MAXT; ++t)
         if (t < ncur) dst[(i64)t * A.out.pstride] = mont_mul(cur[t], fix, m);
 }
 
-cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st) {
-    i64 total = (i64)A.n_batch * A.level * A.N;
-    int blocks = (int)((total + kThreads - 1) / kThreads);
+cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t st) {
+    TensorArgs A = Ain;
+    A.log_n = C.log_n;
+    dim3 blocks((unsigned)(((i64)A.level * A.N + kThreads - 1) / kThreads), A.n_batch);
     count_kernel(C);
-    int in_polys = 0;
-    for (int c = 0; c < A.m; ++c) in_polys += A.child_polys[c];
+    int in_polys = 0, maxt = 0;
+    for (int c = 0; c < A.m; ++c) {
+        in_polys += A.child_polys[c];
+        maxt = std::max(maxt, A.child_polys[c]);
+    }
     int out_polys = in_polys - A.m + 1;
+    maxt = std::max(maxt, out_polys);
     ProfScope ps(C, KC_TENSOR, (double)(in_polys + out_polys) * A.n_batch * A.level * A.N * sizeof(u64), st);
-    tensor_kernel<<<blocks, kThreads, 0, st>>>(A);
+    if (maxt <= 3) tensor_kernel<3><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 4) tensor_kernel<4><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 5) tensor_kernel<5><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 7) tensor_kernel<7><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 9) tensor_kernel<9><<<blocks, kThreads, 0, st>>>(A);
+    else tensor_kernel<CKKS_MAX_TUPLE><<<blocks, kThreads, 0, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -86,6 +97,7 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st
 // y'_j = [y_j (Q_beta/q_j)^-1]_{q_j} was produced by the INTT's epilogue.
 // blockIdx.y = (t, beta) job, blockIdx.z = batch.
 // ---------------------------------------------------------------------------
+template <int AMAX>
 __global__ void __launch_bounds__(kThreads) bconv_kernel(BconvArgs A) {
     extern __shared__ u64 cs[];  // [alpha][n_targets] Montgomery constants
     const int job = blockIdx.y;
@@ -109,19 +121,20 @@ __global__ void __launch_bounds__(kThreads) bconv_kernel(BconvArgs A) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= A.N) return;
     const u64 *ysrc = A.y.ptr + (i64)b * A.y.bstride + (i64)t * A.y.pstride + e;
-    u64 y[16];
+    u64 y[AMAX];
 #pragma unroll
-    for (int jj = 0; jj < 16; ++jj) y[jj] = jj < na ? ysrc[(i64)(d0 + jj) * A.N] : 0ull;
+    for (int jj = 0; jj < AMAX; ++jj) y[jj] = jj < na ? ysrc[(i64)(d0 + jj) * A.N] : 0ull;
     u64 *dst = A.ext.ptr + (i64)b * A.ext.bstride + (i64)(t * A.n_digits + beta) * A.ext.pstride + e;
     for (int ti = 0; ti < n_t; ++ti) {
         const int slot = ti < nq_t ? (ti < d0 ? ti : ti + na) : A.level + (ti - nq_t);
         const int x = ti < nq_t ? slot : A.L + (ti - nq_t);
         const ModQ m = A.mods[x];
-        Acc128 acc;
+        // sum over the digit: hi stays below q because the digit's primes sum to < 2^64
+        Acc128Lazy acc;
         acc.zero();
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj)
-            if (jj < na) acc.mac(y[jj], cs[jj * n_t + ti], m.q);
+        for (int jj = 0; jj < AMAX; ++jj)
+            if (jj < na) acc.mac(y[jj], cs[jj * n_t + ti]);
         dst[(i64)slot * A.N] = redc(acc.hi, acc.lo, m);
     }
 }
@@ -134,7 +147,10 @@ cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) 
     // reads y' once, writes level + K - |digit| limbs per (t, digit)
     double limbs_out = (double)A.n_t * ((double)A.n_digits * (A.level + A.K) - A.level);
     ProfScope ps(C, KC_BCONV, ((double)A.n_t * A.level + limbs_out) * A.n_batch * A.N * sizeof(u64), st);
-    bconv_kernel<<<grid, kThreads, smem, st>>>(A);
+    if (A.alpha <= 4) bconv_kernel<4><<<grid, kThreads, smem, st>>>(A);
+    else if (A.alpha <= 8) bconv_kernel<8><<<grid, kThreads, smem, st>>>(A);
+    else if (A.alpha <= 12) bconv_kernel<12><<<grid, kThreads, smem, st>>>(A);
+    else bconv_kernel<16><<<grid, kThreads, smem, st>>>(A);
     return cudaGetLastError();
 }
 

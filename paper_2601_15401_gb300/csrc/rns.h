@@ -9,7 +9,7 @@ struct Context;
 #define CKKS_MAX_CHILDREN 12
 
 struct TensorArgs {
-    int n_batch, level, N, m;
+    int n_batch, level, N, m, log_n;
     LimbView child[CKKS_MAX_CHILDREN];   // limb j of poly a: ptr + b bstride + a pstride + j N
     int child_polys[CKKS_MAX_CHILDREN];
     LimbView out;
