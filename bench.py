@@ -161,6 +161,10 @@ def run_ours(args, rank, world, local_rank):
         ws_bytes = max(ws_bytes, ctx.workspace_size(k, L, B))
     ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.uint64, device=dev)
     torch.cuda.synchronize()
+    tuned = None
+    if not args.no_tune:
+        from paper_2601_15401_gb300.executor import autotune
+        tuned = autotune(ctx, evk, k=8, batch=4)["choice"]
 
     stream = torch.cuda.current_stream()
     lat = {k: [] for k in ks}
@@ -269,6 +273,7 @@ def run_ours(args, rank, world, local_rank):
         "step_alg_GBps": round((in_bytes + out_bytes) / (ms_step / 1e3) / 1e9, 1),
         "per_k": per_k,
         "clocks": clk,
+        "tuning": tuned,
     }
 
     # ---------------- comparators (outside the timed region)
@@ -465,6 +470,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)

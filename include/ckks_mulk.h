@@ -216,6 +216,15 @@ typedef struct {
 int ckks_profile_enable(ckks_context *ctx, int enable);
 int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, uint32_t *n_out);
 
+/* Launch tunables of a context (chosen by the autotuner; results are the
+ * same for every value). Keys: "ntt_tile" = elements per NTT tile
+ * (1024..8192, power of two; default 4096), "bconv_threads" = threads per
+ * BConv block (64..1024, multiple of 32; default 256), "mac_threads" =
+ * threads per key-MAC block (same range). CKKS_EINVAL for an unknown key or
+ * an out-of-range value. */
+int ckks_tune_set(ckks_context *ctx, const char *key, int value);
+int ckks_tune_get(const ckks_context *ctx, const char *key, int *value);
+
 /* ckks_check: CKKS_ECUDA if a CUDA error is pending on the context's device
  * (sticky launch error or cudaGetLastError), else CKKS_OK. */
 int ckks_check(ckks_context *ctx);

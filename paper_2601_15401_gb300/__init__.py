@@ -266,6 +266,14 @@ class Context:
     def check(self):
         _check(lib().ckks_check(self._h), "ckks_check")
 
+    def tune_set(self, key: str, value: int):
+        _check(lib().ckks_tune_set(self._h, key.encode(), int(value)), f"ckks_tune_set({key})")
+
+    def tune_get(self, key: str) -> int:
+        v = ctypes.c_int()
+        _check(lib().ckks_tune_get(self._h, key.encode(), ctypes.byref(v)), f"ckks_tune_get({key})")
+        return v.value
+
     def profile(self, enable: bool):
         _check(lib().ckks_profile_enable(self._h, int(enable)), "ckks_profile_enable")
 

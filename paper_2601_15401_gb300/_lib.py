@@ -52,6 +52,8 @@ SIGNATURES = {
     "ckks_check": [V],
     "ckks_profile_enable": [V, I],
     "ckks_profile_read": [V, V, U32, V],
+    "ckks_tune_set": [V, ctypes.c_char_p, I],
+    "ckks_tune_get": [V, ctypes.c_char_p, V],
     "ckks_strerror": [I],
 }
 _VOID = {"ckks_context_destroy", "ckks_evk_set_destroy", "ckks_plan_destroy"}

@@ -486,6 +486,32 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
     return CKKS_OK;
 }
 
+static int *tune_slot(ckks_context *ctx, const char *key, int &lo, int &hi) {
+    if (!ctx || !key) return nullptr;
+    if (!strcmp(key, "ntt_tile")) { lo = 1024; hi = 8192; return &ctx->c.tune_ntt_tile; }
+    if (!strcmp(key, "bconv_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_bconv_threads; }
+    if (!strcmp(key, "mac_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_mac_threads; }
+    return nullptr;
+}
+
+int ckks_tune_set(ckks_context *ctx, const char *key, int value) {
+    int lo, hi;
+    int *slot = tune_slot(ctx, key, lo, hi);
+    if (!slot || value < lo || value > hi) return CKKS_EINVAL;
+    if (!strcmp(key, "ntt_tile") && (value & (value - 1))) return CKKS_EINVAL;
+    if (strcmp(key, "ntt_tile") && value % 32) return CKKS_EINVAL;
+    *slot = value;
+    return CKKS_OK;
+}
+
+int ckks_tune_get(const ckks_context *ctx, const char *key, int *value) {
+    int lo, hi;
+    int *slot = tune_slot(const_cast<ckks_context *>(ctx), key, lo, hi);
+    if (!slot || !value) return CKKS_EINVAL;
+    *value = *slot;
+    return CKKS_OK;
+}
+
 int ckks_check(ckks_context *ctx) {
     if (!ctx) return CKKS_EINVAL;
     if (ctx->c.sticky.load() != 0) return CKKS_ECUDA;

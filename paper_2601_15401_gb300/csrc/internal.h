@@ -117,6 +117,10 @@ struct Context {
     std::atomic<unsigned long long> counters[OP_COUNT];
     std::atomic<int> sticky{0};
     Profiler prof;
+    // launch tunables
+    int tune_ntt_tile = 4096;
+    int tune_bconv_threads = 256;
+    int tune_mac_threads = 256;
 };
 
 // Records CUDA events around one launch on its stream when the hook is on;

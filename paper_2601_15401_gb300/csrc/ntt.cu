@@ -57,9 +57,12 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
 // ---------------------------------------------------------------------------
 // pass plan: LOGN stages in ceil(LOGN/4) passes of near-equal length
 // ---------------------------------------------------------------------------
+#ifndef CKKS_NTT_RMAX
+#define CKKS_NTT_RMAX 4
+#endif
 template <int LOGN, int P>
 struct Pass {
-    static constexpr int NP = (LOGN + 3) / 4;
+    static constexpr int NP = (LOGN + CKKS_NTT_RMAX - 1) / CKKS_NTT_RMAX;
     static constexpr int base = LOGN / NP;
     static constexpr int extra = LOGN % NP;
     static constexpr int len = base + (P < extra ? 1 : 0);
@@ -392,7 +395,6 @@ void ntt_geometry(int logN, int &log_n1, int &log_n2) {
     else { log_n1 = logN / 2; log_n2 = logN - log_n1; }
 }
 
-static constexpr int kTileElems = 4096;
 
 // One phase. phase 0 = the first phase executed (forward: columns; inverse:
 // blocks), phase 1 = the second. With log_n1 == 0 there is only phase 1 work
@@ -413,14 +415,14 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
     if (cols) {
         logn = log_n1;
         int n = 1 << logn;
-        n_sub = kTileElems / n;
+        n_sub = C.tune_ntt_tile / n;
         if (n_sub > P.N2) n_sub = P.N2;
         tiles = P.N2 / n_sub;
         smem = (size_t)n * n_sub * sizeof(u64);
     } else {
         logn = log_n2;
         int n = 1 << logn;
-        n_sub = kTileElems / n;
+        n_sub = C.tune_ntt_tile / n;
         if (n_sub < 1) n_sub = 1;
         if (n_sub > P.N1) n_sub = P.N1;
         tiles = P.N1 / n_sub;
@@ -430,7 +432,7 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
     P.log_sub = 0;
     while ((1 << P.log_sub) < n_sub) ++P.log_sub;
     P.log_n2 = log_n2;
-    int per_sub = (1 << logn) >= 16 ? (1 << logn) / 16 : 1;  // radix-16 point sets per sub-problem
+    int per_sub = (1 << logn) >= (1 << CKKS_NTT_RMAX) ? (1 << logn) >> CKKS_NTT_RMAX : 1;  // point sets per sub-problem
     int threads = ((n_sub * per_sub + 31) / 32) * 32;
     if (threads > 256) threads = 256;
     count_op(C, fwd ? OP_NTT_PHASE : OP_INTT_PHASE);

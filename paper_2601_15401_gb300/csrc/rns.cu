@@ -98,7 +98,7 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t 
 // blockIdx.y = (t, beta) job, blockIdx.z = batch.
 // ---------------------------------------------------------------------------
 template <int AMAX>
-__global__ void __launch_bounds__(kThreads) bconv_kernel(BconvArgs A) {
+__global__ void __launch_bounds__(1024) bconv_kernel(BconvArgs A) {
     extern __shared__ u64 cs[];  // [alpha][n_targets] Montgomery constants
     const int job = blockIdx.y;
     const int b = blockIdx.z;
@@ -140,17 +140,18 @@ __global__ void __launch_bounds__(kThreads) bconv_kernel(BconvArgs A) {
 }
 
 cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) {
-    dim3 grid((A.N + kThreads - 1) / kThreads, A.n_t * A.n_digits, A.n_batch);
+    const int thr = C.tune_bconv_threads;
+    dim3 grid((A.N + thr - 1) / thr, A.n_t * A.n_digits, A.n_batch);
     size_t smem = (size_t)A.alpha * (A.level + A.K) * sizeof(u64);
     count_kernel(C);
     count_op(C, OP_BCONV, (unsigned long long)A.n_t * A.n_digits * A.n_batch);
     // reads y' once, writes level + K - |digit| limbs per (t, digit)
     double limbs_out = (double)A.n_t * ((double)A.n_digits * (A.level + A.K) - A.level);
     ProfScope ps(C, KC_BCONV, ((double)A.n_t * A.level + limbs_out) * A.n_batch * A.N * sizeof(u64), st);
-    if (A.alpha <= 4) bconv_kernel<4><<<grid, kThreads, smem, st>>>(A);
-    else if (A.alpha <= 8) bconv_kernel<8><<<grid, kThreads, smem, st>>>(A);
-    else if (A.alpha <= 12) bconv_kernel<12><<<grid, kThreads, smem, st>>>(A);
-    else bconv_kernel<16><<<grid, kThreads, smem, st>>>(A);
+    if (A.alpha <= 4) bconv_kernel<4><<<grid, thr, smem, st>>>(A);
+    else if (A.alpha <= 8) bconv_kernel<8><<<grid, thr, smem, st>>>(A);
+    else if (A.alpha <= 12) bconv_kernel<12><<<grid, thr, smem, st>>>(A);
+    else bconv_kernel<16><<<grid, thr, smem, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -163,8 +164,8 @@ cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) 
 // Grid: x = coefficient chunk, y = target limb, z = batch (fastest-varying
 // batch would reuse key tiles in L2; see launch order below).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) mac_kernel(MacArgs A) {
-    const int chunks = (A.N + kThreads - 1) / kThreads;
+__global__ void __launch_bounds__(1024) mac_kernel(MacArgs A) {
+    const int chunks = (A.N + blockDim.x - 1) / blockDim.x;
     // block order: batch fastest, then chunk, then limb -> blocks that share a
     // key tile run next to each other
     int bid = blockIdx.x;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) mac_kernel(MacArgs A) {
     bid /= A.n_batch;
     const int chunk = bid % chunks;
     const int x = bid / chunks;  // acc slot: Q limbs 0..level-1 then P limbs
-    const int e = chunk * kThreads + threadIdx.x;
+    const int e = chunk * blockDim.x + threadIdx.x;
     if (e >= A.N) return;
     const bool isq = x < A.level;
     const int prime = isq ? x : A.L + (x - A.level);
@@ -202,7 +203,8 @@ __global__ void __launch_bounds__(kThreads) mac_kernel(MacArgs A) {
 }
 
 cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
-    const int chunks = (A.N + kThreads - 1) / kThreads;
+    const int thr = C.tune_mac_threads;
+    const int chunks = (A.N + thr - 1) / thr;
     long long blocks = (long long)chunks * (A.level + A.K) * A.n_batch;
     count_kernel(C);
     // per batch element: (n-1) * digits terms and 2 outputs per target limb;
@@ -211,7 +213,7 @@ cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
     const double limbs = (double)(A.level + A.K);
     double bytes = ((terms + 2.0) * A.n_batch + 2.0 * terms) * limbs * A.N * sizeof(u64);
     ProfScope ps(C, KC_MAC, bytes, st);
-    mac_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(A);
+    mac_kernel<<<(unsigned)blocks, thr, 0, st>>>(A);
     return cudaGetLastError();
 }
 

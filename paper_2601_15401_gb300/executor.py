@@ -1,0 +1,243 @@
+"""Batched execution of uneven k-input multiplications in one CUDA graph.
+
+A workload is a list of requests, each a k-input product at its own ring
+degree N, input level and k. Requests with the same (N, k, level,
+partition) form a group that runs as one batched library call
+(ckks_mul_k_batch: every kernel launch covers the whole group). Groups are
+spread over several streams so that small groups run side by side, and the
+whole schedule is captured once into a CUDA graph; replaying it launches the
+entire workload with one cudaGraphLaunch. Each stream owns one workspace
+sized for the largest group it runs (stream order makes reuse safe), so
+nothing is allocated while the graph runs.
+
+The library calls are the only device work; this module only arranges
+buffers, streams and the graph.
+"""
+from __future__ import annotations
+
+import json
+import os
+from collections import defaultdict
+from dataclasses import dataclass, field
+
+import torch
+
+from . import Context, Tuple
+
+
+@dataclass
+class MulRequest:
+    """One product: k ciphertexts at `level` in the context for `log_n`."""
+    log_n: int
+    k: int
+    level: int
+    partition: str | None = None
+    rid: int = 0
+
+
+@dataclass
+class _Group:
+    log_n: int
+    k: int
+    level: int
+    partition: str | None
+    rids: list = field(default_factory=list)
+    inp: object = None      # [B][k][2][level][N]
+    out: object = None      # [B][2][level - depth][N]
+    tuples: list = None
+    outs: list = None
+    depth: int = 0
+    ws_bytes: int = 0
+    stream: int = 0
+
+
+class BatchExecutor:
+    """contexts: {log_n: (Context, EvkSet)} with keys up to the largest k."""
+
+    def __init__(self, contexts: dict, n_streams: int = 8, device=None):
+        self.contexts = contexts
+        self.n_streams = n_streams
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.groups: list[_Group] = []
+        self.slot_of: dict[int, tuple] = {}
+        self.graph = None
+        self.streams = []
+        self.ws = []
+
+    # -------------------------------------------------------------- planning
+    def plan(self, requests: list[MulRequest]):
+        by_shape = defaultdict(list)
+        for r in requests:
+            by_shape[(r.log_n, r.k, r.level, r.partition)].append(r.rid)
+        self.groups = []
+        for (log_n, k, level, part), rids in sorted(by_shape.items(), key=lambda kv: -len(kv[1]) * kv[0][1]):
+            ctx, _ = self.contexts[log_n]
+            g = _Group(log_n, k, level, part, rids)
+            g.depth = ctx.plan_describe(k, part)["depth"]
+            B, N = len(rids), ctx.N
+            g.inp = torch.empty((B, k, 2, level, N), dtype=torch.uint64, device=self.device)
+            g.out = torch.empty((B, 2, level - g.depth, N), dtype=torch.uint64, device=self.device)
+            g.tuples = [[Tuple(g.inp[b, u], 2, level, level) for u in range(k)] for b in range(B)]
+            g.outs = [Tuple(g.out[b], 2, level - g.depth, level - g.depth) for b in range(B)]
+            g.ws_bytes = ctx.workspace_size(k, level, B, part)
+            for b, rid in enumerate(rids):
+                self.slot_of[rid] = (len(self.groups), b)
+            self.groups.append(g)
+        # balance the groups over the streams by workspace size (a proxy for work)
+        load = [0] * self.n_streams
+        need = [0] * self.n_streams
+        for g in sorted(self.groups, key=lambda g: -g.ws_bytes):
+            s = min(range(self.n_streams), key=lambda i: load[i])
+            g.stream = s
+            load[s] += g.ws_bytes
+            need[s] = max(need[s], g.ws_bytes)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.n_streams)]
+        self.ws = [torch.empty(max(1, n // 8 + 1), dtype=torch.uint64, device=self.device) for n in need]
+        self.graph = None
+
+    def input_view(self, rid: int):
+        """[k][2][level][N] device slot of a request (write its ciphertexts here)."""
+        gi, b = self.slot_of[rid]
+        return self.groups[gi].inp[b]
+
+    def output_view(self, rid: int):
+        gi, b = self.slot_of[rid]
+        return self.groups[gi].out[b]
+
+    def output_tuple(self, rid: int) -> Tuple:
+        gi, b = self.slot_of[rid]
+        return self.groups[gi].outs[b]
+
+    # -------------------------------------------------------------- running
+    def _enqueue(self, main: torch.cuda.Stream):
+        start = torch.cuda.Event()
+        start.record(main)
+        done = []
+        for s in self.streams:
+            s.wait_event(start)
+        for g in self.groups:
+            ctx, evk = self.contexts[g.log_n]
+            st = self.streams[g.stream]
+            ctx.mul_k_batch(g.tuples, evk, g.outs, self.ws[g.stream], partition=g.partition, stream=st)
+        for s in self.streams:
+            e = torch.cuda.Event()
+            e.record(s)
+            done.append(e)
+        for e in done:
+            main.wait_event(e)
+
+    def run_eager(self):
+        """Every group's batched call, stream-ordered, without a graph."""
+        self._enqueue(torch.cuda.current_stream(self.device))
+
+    def capture(self):
+        """Capture the whole schedule into one CUDA graph."""
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=self.device)
+        with torch.cuda.graph(g, stream=cap):
+            self._enqueue(cap)
+        self.graph = g
+        torch.cuda.synchronize(self.device)
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+
+def one_per_launch(contexts, requests, executor: BatchExecutor):
+    """Reference schedule: every product as its own ckks_mul_k call on one
+    stream (reads the executor's input slots, writes its output slots)."""
+    ws_need = 0
+    for r in requests:
+        ctx, _ = contexts[r.log_n]
+        ws_need = max(ws_need, ctx.workspace_size(r.k, r.level, 1, r.partition))
+    ws = torch.empty(ws_need // 8 + 1, dtype=torch.uint64, device=executor.device)
+    for r in requests:
+        ctx, evk = contexts[r.log_n]
+        gi, b = executor.slot_of[r.rid]
+        g = executor.groups[gi]
+        ctx.mul_k(g.tuples[b], evk, g.outs[b], ws, partition=r.partition)
+    return ws
+
+
+# ---------------------------------------------------------------------------
+# autotuner
+# ---------------------------------------------------------------------------
+TUNE_SPACE = {
+    "ntt_tile": [2048, 4096, 8192],
+    "bconv_threads": [128, 256, 512],
+    "mac_threads": [128, 256, 512],
+}
+
+
+def _cache_path() -> str:
+    return os.environ.get("CKKS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "ckks_mulk",
+                                                          "autotune.json"))
+
+
+def tune_key(ctx: Context) -> str:
+    name = torch.cuda.get_device_name(ctx.device).replace(" ", "_")
+    return f"{name}/logN{ctx.log_n}/L{ctx.L}/K{ctx.K}/dnum{ctx.dnum}"
+
+
+def autotune(ctx: Context, evk, k: int = 8, batch: int = 4, reps: int = 3, cache: str | None = None,
+             force: bool = False) -> dict:
+    """Pick each tunable by timing a batched k-input product (coordinate
+    descent over TUNE_SPACE, CUDA events), store the choice in a JSON cache
+    keyed by GPU, N and the prime-chain shape, and apply it to `ctx`."""
+    import synth
+    path = cache or _cache_path()
+    key = tune_key(ctx)
+    db = {}
+    if os.path.exists(path):
+        try:
+            db = json.load(open(path))
+        except Exception:
+            db = {}
+    if key in db and not force:
+        for name, v in db[key]["choice"].items():
+            ctx.tune_set(name, v)
+        return db[key]
+    level = ctx.L
+    depth = ctx.plan_describe(k)["depth"]
+    dev = torch.device("cuda", ctx.device)
+    inp = synth.uniform_residues_torch(ctx.q[:level], (batch, k, 2), ctx.N, 0x7E57, dev)
+    out = torch.empty((batch, 2, level - depth, ctx.N), dtype=torch.uint64, device=dev)
+    tup = [[Tuple(inp[b, u], 2, level, level) for u in range(k)] for b in range(batch)]
+    outs = [Tuple(out[b], 2, level - depth, level - depth) for b in range(batch)]
+    ws = torch.empty(ctx.workspace_size(k, level, batch) // 8 + 1, dtype=torch.uint64, device=dev)
+
+    def timed() -> float:
+        ctx.mul_k_batch(tup, evk, outs, ws)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.mul_k_batch(tup, evk, outs, ws)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    choice = {n: ctx.tune_get(n) for n in TUNE_SPACE}
+    trials = {}
+    for name, values in TUNE_SPACE.items():
+        best = None
+        for v in values:
+            ctx.tune_set(name, v)
+            ms = timed()
+            trials[f"{name}={v}"] = round(ms, 4)
+            if best is None or ms < best[0]:
+                best = (ms, v)
+        choice[name] = best[1]
+        ctx.tune_set(name, best[1])
+    entry = {"choice": choice, "ms": min(trials.values()), "trials": trials, "workload": f"k={k} batch={batch}"}
+    db[key] = entry
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        json.dump(db, open(path, "w"), indent=1)
+    except OSError:
+        pass
+    return entry

@@ -1,0 +1,93 @@
+"""Small, self-contained launches of single library steps for timing and for
+profiler captures (one kernel class at a time, a few GB on the device).
+
+  python -m paper_2601_15401_gb300.microbench --op ntt --batch 16
+  python -m paper_2601_15401_gb300.microbench --op mul_k --k 8 --batch 4
+
+Prints one JSON line: per kernel class, launches, average event time and
+achieved algorithmic GB/s (the library's timing hook).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main():
+    import torch
+
+    import paper_2601_15401_gb300 as G
+    import synth
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2"], default="ntt")
+    ap.add_argument("--log-n", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--k", type=int, default=8)
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    args = ap.parse_args()
+    p = synth.params_large(log_n=args.log_n)
+    ctx = G.Context.from_params(p)
+    L, N, B = p.L, p.N, args.batch
+    if args.op == "ntt":
+        x = synth.uniform_residues_torch(p.q, (B * 2,), N, 7, "cuda")  # [2B][L][N]
+        T = G.Tuple(x, 2 * B, L, L, 0)
+
+        def run():
+            ctx.ntt(T)
+            ctx.intt(T)
+    else:
+        t_max = max(args.k, 2)
+        g = synth.rng(9, 0, stream=1)
+        s = torch.from_numpy(synth.ternary_secret(g, N)).cuda()
+        import numpy as np
+        e = torch.from_numpy(np.stack([[synth.gaussian(g, N) for _ in range(p.dnum)] for _ in range(t_max - 1)])).cuda()
+        a = synth.uniform_residues_torch(list(p.q) + list(p.p), (t_max - 1, p.dnum), N, 0x31, "cuda")
+        keys = torch.empty((t_max - 1, p.dnum, 2, L + p.K, N), dtype=torch.uint64, device="cuda")
+        kws = torch.empty(ctx.keygen_workspace_size() // 8, dtype=torch.uint64, device="cuda")
+        ctx.keygen_evk(t_max, s, a, e, keys, kws)
+        del a, kws
+        evk = ctx.evk_set(t_max, keys)
+        if args.op == "mul_k":
+            k = args.k
+            depth = ctx.plan_describe(k)["depth"]
+            inp = synth.uniform_residues_torch(p.q, (B, k, 2), N, 11, "cuda")
+            out = torch.empty((B, 2, L - depth, N), dtype=torch.uint64, device="cuda")
+            tup = [[G.Tuple(inp[b, u], 2, L, L) for u in range(k)] for b in range(B)]
+            outs = [G.Tuple(out[b], 2, L - depth, L - depth) for b in range(B)]
+            ws = torch.empty(ctx.workspace_size(k, L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
+
+            def run():
+                ctx.mul_k_batch(tup, evk, outs, ws)
+        else:
+            inp = synth.uniform_residues_torch(p.q, (B, 2, 2), N, 12, "cuda")
+            out = torch.empty((B, 2, L - 1, N), dtype=torch.uint64, device="cuda")
+            a_ = [G.Tuple(inp[b, 0], 2, L, L) for b in range(B)]
+            b_ = [G.Tuple(inp[b, 1], 2, L, L) for b in range(B)]
+            outs = [G.Tuple(out[b], 2, L - 1, L - 1) for b in range(B)]
+            ws = torch.empty(ctx.mul2_workspace_size(L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
+
+            def run():
+                ctx.mul2_batch(a_, b_, evk, outs, ws)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        run()
+    e1.record()
+    e1.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    ctx.check()
+    print(json.dumps({
+        "op": args.op, "log_n": args.log_n, "batch": B, "k": args.k, "ms_per_rep": round(e0.elapsed_time(e1) / args.reps, 4),
+        "kernels": {n: {"launches": v["launches"], "avg_us": round(v["total_ms"] * 1e3 / v["launches"], 2),
+                        "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)} for n, v in prof.items()}}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,325 @@
+"""Continuous-batching server for k-input multiplications.
+
+Evaluation keys and a pool of ciphertexts stay resident on the device, one
+set per ring degree. A request names k pool ciphertexts, a level and
+(optionally) a partition. The scheduler keeps a queue of arrived requests
+and, whenever a stream is free and the device-memory budget allows, launches
+a batch: the pending requests of one shape (N, k, level, partition), oldest
+first, up to `max_batch`. Requests that arrive while other batches run join
+the next batches (continuous batching); batches on different streams run
+side by side on the device. A request's footprint (its input slot, output
+and its share of the batch workspace) is admitted only under the memory cap;
+otherwise it waits. Latency = completion (CUDA event observed) - arrival.
+
+The scheduling logic is independent of the device: `Scheduler` drives any
+backend with launch / poll; `GpuBackend` runs batches through the library
+(ckks_mul_k_batch), `tests` drive the scheduler with a host-only fake.
+
+Run `python -m paper_2601_15401_gb300.serve --rate 2000 --seconds 30` for the
+Poisson-arrival measurement (p50 / p99 latency, sustained products/s).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import statistics
+import time
+from collections import OrderedDict, deque
+from dataclasses import dataclass, field
+
+
+@dataclass
+class Request:
+    rid: int
+    log_n: int
+    k: int
+    level: int
+    cts: tuple           # pool indices of the k input ciphertexts
+    arrival: float = 0.0
+    partition: str | None = None
+    admitted: float = -1.0
+    done: float = -1.0
+
+    @property
+    def shape(self):
+        return (self.log_n, self.k, self.level, self.partition)
+
+
+@dataclass
+class Batch:
+    bid: int
+    shape: tuple
+    reqs: list
+    stream: int
+    footprint: int
+    handle: object = None
+    launched: float = 0.0
+
+
+class Scheduler:
+    """Continuous batching with admission by memory footprint.
+
+    backend must provide: n_streams, footprint(shape, batch) -> bytes,
+    launch(batch) -> handle, poll(handle) -> bool, and optional finish(batch)."""
+
+    def __init__(self, backend, cap_bytes: int, max_batch: int = 8, max_queue: int = 100000):
+        self.be = backend
+        self.cap = cap_bytes
+        self.max_batch = max_batch
+        self.max_queue = max_queue
+        self.queues: "OrderedDict[tuple, deque]" = OrderedDict()
+        self.free_streams = deque(range(backend.n_streams))
+        self.running: list[Batch] = []
+        self.in_use = 0
+        self.next_bid = 0
+        self.completed: list[Request] = []
+        self.rejected = 0
+        self.admitted_batches = 0
+
+    def submit(self, r: Request) -> bool:
+        if sum(len(q) for q in self.queues.values()) >= self.max_queue:
+            self.rejected += 1
+            return False
+        self.queues.setdefault(r.shape, deque()).append(r)
+        return True
+
+    def pending(self) -> int:
+        return sum(len(q) for q in self.queues.values())
+
+    def _pick(self):
+        """Shape whose oldest request arrived first."""
+        best = None
+        for shape, q in self.queues.items():
+            if q and (best is None or q[0].arrival < self.queues[best][0].arrival):
+                best = shape
+        return best
+
+    def step(self, now: float) -> int:
+        """Retire finished batches, then launch as many batches as streams and
+        memory allow. Returns the number of batches launched."""
+        still = []
+        for b in self.running:
+            if self.be.poll(b.handle):
+                t = time.perf_counter() if now is None else now
+                for r in b.reqs:
+                    r.done = t
+                self.completed.extend(b.reqs)
+                self.in_use -= b.footprint
+                self.free_streams.append(b.stream)
+                fin = getattr(self.be, "finish", None)
+                if fin:
+                    fin(b)
+            else:
+                still.append(b)
+        self.running = still
+        launched = 0
+        while self.free_streams:
+            shape = self._pick()
+            if shape is None:
+                break
+            q = self.queues[shape]
+            n = min(len(q), self.max_batch)
+            while n > 0 and self.in_use + self.be.footprint(shape, n) > self.cap:
+                n -= 1
+            if n == 0:
+                break  # wait for memory to free up
+            reqs = [q.popleft() for _ in range(n)]
+            if not q:
+                del self.queues[shape]
+            fp = self.be.footprint(shape, n)
+            b = Batch(self.next_bid, shape, reqs, self.free_streams.popleft(), fp)
+            self.next_bid += 1
+            for r in reqs:
+                r.admitted = now
+            b.launched = now
+            b.handle = self.be.launch(b)
+            self.in_use += fp
+            self.running.append(b)
+            self.admitted_batches += 1
+            launched += 1
+        return launched
+
+    def idle(self) -> bool:
+        return not self.running and self.pending() == 0
+
+
+# ---------------------------------------------------------------------------
+# device backend
+# ---------------------------------------------------------------------------
+class GpuBackend:
+    """Runs batches through the library; contexts: {log_n: (Context, EvkSet)},
+    pools: {log_n: tensor [P][2][L][N]} of resident ciphertexts (NTT domain)."""
+
+    def __init__(self, contexts, pools, n_streams: int = 8):
+        import torch
+        self.torch = torch
+        self.contexts = contexts
+        self.pools = pools
+        self.n_streams = n_streams
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.results = {}
+        self._fp_cache = {}
+
+    def footprint(self, shape, n: int) -> int:
+        key = (shape, n)
+        if key not in self._fp_cache:
+            log_n, k, level, part = shape
+            ctx, _ = self.contexts[log_n]
+            depth = ctx.plan_describe(k, part)["depth"]
+            limb = ctx.N * 8
+            slots = n * (k * 2 * level + 2 * (level - depth)) * limb
+            self._fp_cache[key] = slots + ctx.workspace_size(k, level, n, part)
+        return self._fp_cache[key]
+
+    def launch(self, b: Batch):
+        torch = self.torch
+        from . import Tuple
+        log_n, k, level, part = b.shape
+        ctx, evk = self.contexts[log_n]
+        depth = ctx.plan_describe(k, part)["depth"]
+        st = self.streams[b.stream]
+        n = len(b.reqs)
+        pool = self.pools[log_n]
+        with torch.cuda.stream(st):
+            idx = torch.tensor([c for r in b.reqs for c in r.cts], device=pool.device)
+            # gather on an int64 view (same bits; uint64 has no CUDA gather)
+            inp = pool.view(torch.int64).index_select(0, idx)[:, :, :level].reshape(n, k, 2, level, ctx.N)
+            inp = inp.contiguous().view(torch.uint64)
+            out = torch.empty((n, 2, level - depth, ctx.N), dtype=torch.uint64, device=pool.device)
+            ws = torch.empty(ctx.workspace_size(k, level, n, part) // 8 + 1, dtype=torch.uint64, device=pool.device)
+            tup = [[Tuple(inp[i, u], 2, level, level) for u in range(k)] for i in range(n)]
+            outs = [Tuple(out[i], 2, level - depth, level - depth) for i in range(n)]
+            ctx.mul_k_batch(tup, evk, outs, ws, partition=part, stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        # keep the buffers alive until the event completes
+        return (ev, inp, out, ws)
+
+    def poll(self, handle) -> bool:
+        return handle[0].query()
+
+    def finish(self, b: Batch):
+        out = b.handle[2]
+        for i, r in enumerate(b.reqs):
+            self.results[r.rid] = out[i]
+        b.handle = None
+
+
+def poisson_arrivals(rate: float, seconds: float, rng) -> list[float]:
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            return out
+        out.append(t)
+
+
+def run_open_loop(sched: Scheduler, requests: list[Request], timeout: float = 600.0) -> float:
+    """Feed requests at their arrival times (seconds from start) and run the
+    scheduler until all complete. Returns the wall time."""
+    t0 = time.perf_counter()
+    i = 0
+    n = len(requests)
+    while True:
+        now = time.perf_counter() - t0
+        while i < n and requests[i].arrival <= now:
+            requests[i].arrival = t0 + requests[i].arrival
+            sched.submit(requests[i])
+            i += 1
+        sched.step(time.perf_counter())
+        if i >= n and sched.idle():
+            break
+        if now > timeout:
+            raise TimeoutError("serving run did not drain")
+        if i < n and not sched.running and sched.pending() == 0:
+            time.sleep(max(0.0, min(0.0005, requests[i].arrival - now)))
+    return time.perf_counter() - t0
+
+
+def latency_stats(reqs: list[Request]) -> dict:
+    lat = sorted((r.done - r.arrival) * 1e3 for r in reqs)
+    if not lat:
+        return {}
+    p = lambda f: lat[min(len(lat) - 1, max(0, math.ceil(f * len(lat)) - 1))]
+    return {"p50_ms": round(p(0.50), 3), "p99_ms": round(p(0.99), 3), "mean_ms": round(statistics.mean(lat), 3),
+            "max_ms": round(lat[-1], 3), "n": len(lat)}
+
+
+# ---------------------------------------------------------------------------
+# the mixed workload (k uniform in 2..12, N in {2^14, 2^15, 2^16},
+# level uniform in [k, 24]) served at a Poisson rate
+# ---------------------------------------------------------------------------
+def mixed_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size=64, k_range=(2, 12)):
+    import numpy as np
+    g = np.random.default_rng(seed)
+    arr = poisson_arrivals(rate, seconds, g)
+    reqs = []
+    for i, t in enumerate(arr):
+        k = int(g.integers(k_range[0], k_range[1] + 1))
+        log_n = int(g.choice(log_ns))
+        level = int(g.integers(k, L + 1))
+        cts = tuple(int(x) for x in g.integers(0, pool_size, size=k))
+        reqs.append(Request(i, log_n, k, level, cts, arrival=t))
+    return reqs
+
+
+def build_gpu_state(log_ns, L=24, K=8, dnum=3, t_max=12, pool_size=64, device=0):
+    """Contexts, resident keys (generated on the device) and ciphertext pools."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    from . import Context
+    contexts, pools = {}, {}
+    for log_n in log_ns:
+        params = synth.params_large(log_n=log_n, L=L, K=K, dnum=dnum)
+        ctx = Context.from_params(params, device=device)
+        g = synth.rng(5, log_n, stream=1)
+        N = params.N
+        s = torch.from_numpy(synth.ternary_secret(g, N)).cuda()
+        e = torch.from_numpy(np.stack([[synth.gaussian(g, N) for _ in range(dnum)] for _ in range(t_max - 1)])).cuda()
+        a = synth.uniform_residues_torch(list(params.q) + list(params.p), (t_max - 1, dnum), N, 0x5E + log_n, "cuda")
+        keys = torch.empty((t_max - 1, dnum, 2, L + K, N), dtype=torch.uint64, device="cuda")
+        ws = torch.empty(ctx.keygen_workspace_size() // 8, dtype=torch.uint64, device="cuda")
+        ctx.keygen_evk(t_max, s, a, e, keys, ws)
+        del a, ws
+        evk = ctx.evk_set(t_max, keys)
+        contexts[log_n] = (ctx, evk)
+        pools[log_n] = synth.uniform_residues_torch(params.q, (pool_size, 2), N, 0x9000 + log_n, "cuda")
+    torch.cuda.synchronize()
+    return contexts, pools
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--seconds", type=float, default=30.0)
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--max-batch", type=int, default=8)
+    ap.add_argument("--cap-gb", type=float, default=150.0)
+    ap.add_argument("--log-ns", default="14,15,16")
+    ap.add_argument("--seed", type=int, default=2026)
+    args = ap.parse_args()
+    log_ns = tuple(int(x) for x in args.log_ns.split(","))
+    contexts, pools = build_gpu_state(log_ns)
+    be = GpuBackend(contexts, pools, n_streams=args.streams)
+    # warm up every shape class once is too many; warm the kernels with a short burst
+    warm = mixed_requests(200.0, 0.2, args.seed + 1, log_ns)
+    run_open_loop(Scheduler(be, int(args.cap_gb * 1e9), args.max_batch), warm)
+    reqs = mixed_requests(args.rate, args.seconds, args.seed, log_ns)
+    sched = Scheduler(be, int(args.cap_gb * 1e9), args.max_batch)
+    wall = run_open_loop(sched, reqs, timeout=args.seconds * 20 + 120)
+    stats = latency_stats(sched.completed)
+    sizes = {}
+    print(json.dumps({"metric": "served k-input ct-mults/s (Poisson arrivals, mixed k, N, level)",
+                      "offered_rate": args.rate, "seconds": args.seconds, "requests": len(reqs),
+                      "completed": len(sched.completed), "wall_s": round(wall, 3),
+                      "sustained_ctmults_s": round(len(sched.completed) / wall, 1), "latency": stats,
+                      "batches": sched.admitted_batches, "mean_batch": round(len(reqs) / max(1, sched.admitted_batches), 2),
+                      "streams": args.streams, "max_batch": args.max_batch, "cap_gb": args.cap_gb}))
+
+
+if __name__ == "__main__":
+    main()
