@@ -190,6 +190,24 @@ int ckks_rescale_workspace_size(const ckks_context *ctx, uint32_t n_polys, uint3
 int ckks_rescale_multi(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckks_tuple *out, void *workspace,
                        size_t ws_bytes, void *stream);
 
+/* ckks_rescale_multi_noalloc: the same result as ckks_rescale_multi, for
+ * callers that cannot allocate device memory where they need a rescale
+ * (inside someone else's stream capture, in a loop that forbids allocator
+ * calls, or in a component that only receives device pointers). The paper
+ * has no counterpart: this is an interface for such callers. Its scratch is
+ * a fixed device array inside the library, ckks_rescale_noalloc_capacity()
+ * bytes (32 MiB), held on every device that loads the library until exit;
+ * the call makes no cudaMalloc / cudaFree or other allocation. Inputs and
+ * outputs are still the caller's (in and out may be the same tuple).
+ * The first call on a device resolves the array's device address (once per
+ * device, that device made current); make that first call before any stream
+ * capture. Sizes whose scratch exceeds the capacity are rejected with
+ * CKKS_ENOMEM. All calls share the one array: calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race and must be
+ * ordered by the caller. Keep the timing hook off during these calls. */
+size_t ckks_rescale_noalloc_capacity(void);
+int ckks_rescale_multi_noalloc(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckks_tuple *out, void *stream);
+
 /* Forward / inverse transform of every limb of a tuple (in and out may be
  * the same tuple); sets out->ntt_form. */
 int ckks_ntt(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *stream);

@@ -243,6 +243,19 @@ class Context:
         out.level, out.n_polys, out.ntt_form, out.scale, out.poly_stride = o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride
         return out
 
+    def rescale_multi_noalloc(self, t: Tuple, mu: int, out: Tuple, stream=None) -> Tuple:
+        """Algorithm 1 with the library's fixed scratch array (no workspace,
+        no allocation); see ckks_rescale_multi_noalloc in the header."""
+        ci, o = t.c(), out.c()
+        _check(lib().ckks_rescale_multi_noalloc(self._h, ctypes.byref(ci), mu, ctypes.byref(o), _stream(stream)),
+               "ckks_rescale_multi_noalloc")
+        out.level, out.n_polys, out.ntt_form, out.scale, out.poly_stride = o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride
+        return out
+
+    @staticmethod
+    def rescale_noalloc_capacity() -> int:
+        return lib().ckks_rescale_noalloc_capacity()
+
     def ntt(self, t: Tuple, out: Tuple | None = None, stream=None) -> Tuple:
         out = out or t
         ci, o = t.c(), out.c()

@@ -46,6 +46,8 @@ SIGNATURES = {
     "ckks_relin": [V, V, V, U32, V, V, SZ, V],
     "ckks_rescale_workspace_size": [V, U32, U32, U32, V],
     "ckks_rescale_multi": [V, V, U32, V, V, SZ, V],
+    "ckks_rescale_noalloc_capacity": [],
+    "ckks_rescale_multi_noalloc": [V, V, U32, V, V],
     "ckks_ntt": [V, V, V, V],
     "ckks_intt": [V, V, V, V],
     "ckks_counters": [V, V, I],
@@ -58,6 +60,7 @@ SIGNATURES = {
 }
 _VOID = {"ckks_context_destroy", "ckks_evk_set_destroy", "ckks_plan_destroy"}
 _STR = {"ckks_strerror"}
+_SIZE = {"ckks_rescale_noalloc_capacity"}
 
 
 @lru_cache(maxsize=1)
@@ -70,5 +73,6 @@ def lib() -> ctypes.CDLL:
     for name, args in SIGNATURES.items():
         f = getattr(L, name)
         f.argtypes = args
-        f.restype = None if name in _VOID else (ctypes.c_char_p if name in _STR else ctypes.c_int)
+        f.restype = None if name in _VOID else (ctypes.c_char_p if name in _STR else
+                                                (ctypes.c_size_t if name in _SIZE else ctypes.c_int))
     return L

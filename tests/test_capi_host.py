@@ -23,7 +23,7 @@ def L():
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "ckks_mulk.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(ckks_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|size_t|const char \*)\s*\*?\s*(ckks_\w+)\s*\(", text, flags=re.M)))
 
 
 def test_every_declared_symbol_is_exported(L):
