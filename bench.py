@@ -168,8 +168,25 @@ def run_ours(args, rank, world, local_rank):
 
     stream = torch.cuda.current_stream()
     lat = {k: [] for k in ks}
+    ex = None
+    if args.streams > 1:
+        # the step through the batched executor: one group per k, groups
+        # spread over streams, the whole step captured in one CUDA graph
+        from paper_2601_15401_gb300.executor import BatchExecutor, MulRequest
+        ex = BatchExecutor({16: (ctx, evk)}, n_streams=args.streams, device=dev)
+        reqs = [MulRequest(16, k, L, None, 1000 * k + b) for k in ks for b in range(B)]
+        ex.plan(reqs)
+        for k in ks:
+            gi = ex.slot_of[1000 * k][0]
+            ex.groups[gi].inp.copy_(inp[k])
+        ws = None
+        torch.cuda.empty_cache()
+        ex.capture()
 
     def step(record=False):
+        if ex is not None:
+            ex.replay()
+            return []
         evs = []
         for k in ks:
             if record:
@@ -245,7 +262,9 @@ def run_ours(args, rank, world, local_rank):
                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
                     "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
-                    "avg_launch_us": st["total_ms"] * 1e3 / st["launches"]}
+                    "avg_launch_us": st["total_ms"] * 1e3 / st["launches"],
+                    "limiter": "integer multiply (fmaheavy) pipe, not HBM: ncu shows it 55-83 % busy with "
+                               "math-pipe throttle as the top stall (profiles/)"}
     kernel_table = {n: {"launches": v["launches"] // args.steps, "ms_per_step": round(v["total_ms"] / args.steps, 3),
                         "share": round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4),
                         "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)}
@@ -253,10 +272,10 @@ def run_ours(args, rank, world, local_rank):
     # whole-step algorithmic bytes: inputs + outputs + keys once per step
     in_bytes = sum(B * k * 2 * L * N * 8 for k in ks)
     out_bytes = sum(B * 2 * (L - depth[k]) * N * 8 for k in ks)
-    lat_all = [x for k in ks for x in lat[k]]
+    lat_all = [x for k in ks for x in lat[k]] or [ms_step]
     per_k = {}
     for k in ks:
-        xs = sorted(lat[k])
+        xs = sorted(lat[k]) or [float("nan")]
         per_k[k] = {"batch_ms_p50": round(statistics.median(xs), 3), "kinput_ctmults_s": round(B / (statistics.median(xs) / 1e3), 1)}
 
     result = {
@@ -264,7 +283,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded uniform residues, seeded key draws)",
         "config": dict(CONFIG, ks=ks, batch_per_k=B, products_per_step=B * len(ks),
-                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       executor=f"CUDA graph, {args.streams} streams" if args.streams > 1 else "one stream, eager"),
         "gpu_launches": int(launches),
         "latency_ms": {"per_batch_p50": round(statistics.median(lat_all), 3),
                        "per_batch_p99": round(sorted(lat_all)[max(0, math.ceil(0.99 * len(lat_all)) - 1)], 3)},
@@ -302,7 +322,9 @@ def run_ours(args, rank, world, local_rank):
 
     # ---------------- end to end through the C ABI with host buffers
     if not args.no_e2e:
-        result["e2e"] = e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, inp[max(ks)])
+        if ex is None:
+            result["e2e"] = e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, inp, outs, tup, otup,
+                                    inp[max(ks)].clone())
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(args)
@@ -348,29 +370,41 @@ def chained_ms(ctx, evk, inp, k, B, L, N, dev, stream, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, src):
-    """Same step through the C ABI, with the inputs copied from pinned host
-    memory and the outputs copied back to it inside the timed region."""
+def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp, dev_out, tup, otup, src):
+    """The step through the C ABI with host buffers: every k's inputs are
+    copied from pinned host memory, multiplied, and the outputs copied back,
+    all inside the timed region. Copies run on a second stream so that the
+    upload of k+1 overlaps the multiply of k (each k has its own device
+    buffers); the download of k waits for its multiply."""
     import torch
-
-    import paper_2601_15401_gb300 as G
     kmax = max(ks)
     host_in = torch.empty((B, kmax, 2, L, N), dtype=torch.uint64, pin_memory=True)
     host_in.copy_(src)  # the step's synthetic inputs, staged in pinned host memory
     host_out = {k: torch.empty((B, 2, L - depth[k], N), dtype=torch.uint64, pin_memory=True) for k in ks}
-    dev_in = torch.empty((B, kmax, 2, L, N), dtype=torch.uint64, device=dev)
-    dev_out = {k: torch.empty((B, 2, L - depth[k], N), dtype=torch.uint64, device=dev) for k in ks}
-    tup = {k: [[G.Tuple(dev_in[b, u], 2, L, L) for u in range(k)] for b in range(B)] for k in ks}
-    otup = {k: [G.Tuple(dev_out[k][b], 2, L - depth[k], L - depth[k]) for b in range(B)] for k in ks}
     h2d = sum(B * k * 2 * L * N * 8 for k in ks)
     d2h = sum(B * 2 * (L - depth[k]) * N * 8 for k in ks)
+    copy = torch.cuda.Stream(device=dev)
 
     def step():
+        up = {}
         for k in ks:
-            for b in range(B):
-                dev_in[b, :k].copy_(host_in[b, :k], non_blocking=True)
+            with torch.cuda.stream(copy):
+                for b in range(B):
+                    dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
+                e = torch.cuda.Event()
+                e.record(copy)
+                up[k] = e
+        for k in ks:
+            stream.wait_event(up[k])
             ctx.mul_k_batch(tup[k], evk, otup[k], ws, stream=stream)
-            host_out[k].copy_(dev_out[k], non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(stream)
+            copy.wait_event(done)
+            with torch.cuda.stream(copy):
+                host_out[k].copy_(dev_out[k], non_blocking=True)
+        fin = torch.cuda.Event()
+        fin.record(copy)
+        stream.wait_event(fin)
 
     for _ in range(max(1, args.warmup)):
         step()
@@ -383,13 +417,24 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, src):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # upload bandwidth alone, for context
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(copy)
+    with torch.cuda.stream(copy):
+        for k in ks:
+            for b in range(B):
+                dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
+    t1.record(copy)
+    t1.synchronize()
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms = float(tt.item())
     ctx.check()
     return {"value": round(B * len(ks) * world / (ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3)}
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
+            "h2d_GBps_alone": round(h2d / (t0.elapsed_time(t1) / 1e3) / 1e9, 1),
+            "overlap": "uploads on a copy stream overlap the multiplies"}
 
 
 # ---------------------------------------------------------------------------
@@ -471,6 +516,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--streams", type=int, default=1)
     args = ap.parse_args()
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
