@@ -241,3 +241,78 @@ def autotune(ctx: Context, evk, k: int = 8, batch: int = 4, reps: int = 3, cache
     except OSError:
         pass
     return entry
+
+
+# ---------------------------------------------------------------------------
+# the uneven-batch measurement: 1024 products with k uniform in 2..12, N in
+# {2^14, 2^15, 2^16}, input level uniform in [k, 24], in one graph launch
+# ---------------------------------------------------------------------------
+def main():
+    import argparse
+    import numpy as np
+
+    from .serve import build_gpu_state
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=1024)
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--log-ns", default="14,15,16")
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--no-tune", action="store_true")
+    args = ap.parse_args()
+    log_ns = [int(x) for x in args.log_ns.split(",")]
+    contexts, pools = build_gpu_state(tuple(log_ns))
+    tuned = {}
+    if not args.no_tune:
+        for ln, (ctx, evk) in contexts.items():
+            tuned[ln] = autotune(ctx, evk, k=8, batch=4)["choice"]
+    g = np.random.default_rng(args.seed)
+    reqs, srcs = [], {}
+    for i in range(args.requests):
+        k = int(g.integers(2, 13))
+        log_n = int(g.choice(log_ns))
+        level = int(g.integers(k, 25))
+        reqs.append(MulRequest(log_n, k, level, None, i))
+        srcs[i] = [int(x) for x in g.integers(0, pools[log_n].shape[0], size=k)]
+    ex = BatchExecutor(contexts, n_streams=args.streams)
+    ex.plan(reqs)
+    for r in reqs:
+        src = pools[r.log_n].view(torch.int64)[srcs[r.rid]][:, :, :r.level]
+        ex.input_view(r.rid).view(torch.int64).copy_(src)
+    torch.cuda.synchronize()
+    t_cap = torch.cuda.Event(enable_timing=True)
+    ex.capture()
+    ex.replay()  # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        ex.replay()
+    e1.record()
+    e1.synchronize()
+    graph_ms = e0.elapsed_time(e1) / args.reps
+    graph_out = {r.rid: ex.output_view(r.rid).clone() for r in reqs}
+    # reference schedule: one product per library call, one stream, eager
+    ws = one_per_launch(contexts, reqs, ex)  # warm
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.reps):
+        one_per_launch(contexts, reqs, ex)
+    e1.record()
+    e1.synchronize()
+    single_ms = e0.elapsed_time(e1) / args.reps
+    same = all(torch.equal(graph_out[r.rid].view(torch.int64), ex.output_view(r.rid).view(torch.int64)) for r in reqs)
+    kernels = sum(len(g.tuples) > 0 for g in ex.groups)
+    print(json.dumps({
+        "workload": f"{args.requests} k-input products, k in 2..12, N in {[1 << x for x in log_ns]}, level in [k, 24], "
+                    "L=24x50-bit q, K=8x60-bit p, dnum=3",
+        "groups": len(ex.groups), "streams": args.streams,
+        "graph_ms": round(graph_ms, 3), "graph_ctmults_s": round(args.requests / (graph_ms / 1e3), 1),
+        "one_per_launch_ms": round(single_ms, 3),
+        "one_per_launch_ctmults_s": round(args.requests / (single_ms / 1e3), 1),
+        "speedup": round(single_ms / graph_ms, 3), "results_identical": bool(same), "tuning": tuned}))
+
+
+if __name__ == "__main__":
+    main()

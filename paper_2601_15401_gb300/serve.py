@@ -120,7 +120,8 @@ class Scheduler:
                 break
             q = self.queues[shape]
             n = min(len(q), self.max_batch)
-            while n > 0 and self.in_use + self.be.footprint(shape, n) > self.cap:
+            fits = getattr(self.be, "fits", None)
+            while n > 0 and (self.in_use + self.be.footprint(shape, n) > self.cap or (fits and not fits(shape, n))):
                 n -= 1
             if n == 0:
                 break  # wait for memory to free up
@@ -149,27 +150,46 @@ class Scheduler:
 # ---------------------------------------------------------------------------
 class GpuBackend:
     """Runs batches through the library; contexts: {log_n: (Context, EvkSet)},
-    pools: {log_n: tensor [P][2][L][N]} of resident ciphertexts (NTT domain)."""
+    pools: {log_n: tensor [P][2][L][N]} of resident ciphertexts (NTT domain).
 
-    def __init__(self, contexts, pools, n_streams: int = 8):
+    Every stream owns one workspace of `ws_bytes` allocated up front, so a
+    batch allocates only its gathered inputs and its outputs; a shape whose
+    workspace for n requests exceeds `ws_bytes` runs with fewer requests."""
+
+    def __init__(self, contexts, pools, n_streams: int = 8, ws_bytes: int = 4 << 30, keep_results: bool = False):
         import torch
         self.torch = torch
+        self.keep_results = keep_results
         self.contexts = contexts
         self.pools = pools
         self.n_streams = n_streams
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.ws_bytes = ws_bytes
+        self.ws = [torch.empty(ws_bytes // 8, dtype=torch.uint64, device="cuda") for _ in range(n_streams)]
         self.results = {}
         self._fp_cache = {}
+        self._ws_cache = {}
+
+    def resident_bytes(self) -> int:
+        """Keys, pools, contexts' tables and the stream workspaces."""
+        return self.torch.cuda.memory_allocated()
+
+    def fits(self, shape, n: int) -> bool:
+        key = (shape, n)
+        if key not in self._ws_cache:
+            log_n, k, level, part = shape
+            ctx, _ = self.contexts[log_n]
+            self._ws_cache[key] = ctx.workspace_size(k, level, n, part)
+        return self._ws_cache[key] <= self.ws_bytes
 
     def footprint(self, shape, n: int) -> int:
+        """Device bytes a batch allocates: gathered inputs and outputs."""
         key = (shape, n)
         if key not in self._fp_cache:
             log_n, k, level, part = shape
             ctx, _ = self.contexts[log_n]
             depth = ctx.plan_describe(k, part)["depth"]
-            limb = ctx.N * 8
-            slots = n * (k * 2 * level + 2 * (level - depth)) * limb
-            self._fp_cache[key] = slots + ctx.workspace_size(k, level, n, part)
+            self._fp_cache[key] = n * (k * 2 * level + 2 * (level - depth)) * ctx.N * 8
         return self._fp_cache[key]
 
     def launch(self, b: Batch):
@@ -183,26 +203,29 @@ class GpuBackend:
         pool = self.pools[log_n]
         with torch.cuda.stream(st):
             idx = torch.tensor([c for r in b.reqs for c in r.cts], device=pool.device)
-            # gather on an int64 view (same bits; uint64 has no CUDA gather)
-            inp = pool.view(torch.int64).index_select(0, idx)[:, :, :level].reshape(n, k, 2, level, ctx.N)
-            inp = inp.contiguous().view(torch.uint64)
+            # gather only the active limbs, on an int64 view (same bits; uint64
+            # has no CUDA gather)
+            inp = pool.view(torch.int64)[:, :, :level].index_select(0, idx).view(torch.uint64)
+            inp = inp.view(n, k, 2, level, ctx.N)
             out = torch.empty((n, 2, level - depth, ctx.N), dtype=torch.uint64, device=pool.device)
-            ws = torch.empty(ctx.workspace_size(k, level, n, part) // 8 + 1, dtype=torch.uint64, device=pool.device)
             tup = [[Tuple(inp[i, u], 2, level, level) for u in range(k)] for i in range(n)]
             outs = [Tuple(out[i], 2, level - depth, level - depth) for i in range(n)]
-            ctx.mul_k_batch(tup, evk, outs, ws, partition=part, stream=st)
+            ctx.mul_k_batch(tup, evk, outs, self.ws[b.stream], partition=part, stream=st)
             ev = torch.cuda.Event()
             ev.record(st)
         # keep the buffers alive until the event completes
-        return (ev, inp, out, ws)
+        return (ev, inp, out)
 
     def poll(self, handle) -> bool:
         return handle[0].query()
 
     def finish(self, b: Batch):
-        out = b.handle[2]
-        for i, r in enumerate(b.reqs):
-            self.results[r.rid] = out[i]
+        """Completed batch: hand results over (kept only when asked; a
+        served result otherwise goes back to the allocator)."""
+        if self.keep_results:
+            out = b.handle[2]
+            for i, r in enumerate(b.reqs):
+                self.results[r.rid] = out[i]
         b.handle = None
 
 
@@ -299,17 +322,23 @@ def main():
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--max-batch", type=int, default=8)
     ap.add_argument("--cap-gb", type=float, default=150.0)
+    ap.add_argument("--ws-gb", type=float, default=6.0)
     ap.add_argument("--log-ns", default="14,15,16")
     ap.add_argument("--seed", type=int, default=2026)
     args = ap.parse_args()
     log_ns = tuple(int(x) for x in args.log_ns.split(","))
     contexts, pools = build_gpu_state(log_ns)
-    be = GpuBackend(contexts, pools, n_streams=args.streams)
-    # warm up every shape class once is too many; warm the kernels with a short burst
+    be = GpuBackend(contexts, pools, n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)))
+    # the cap covers everything on the device: keys, pools, tables and stream
+    # workspaces are resident; batches are admitted within what is left
+    resident = be.resident_bytes()
+    budget = int(args.cap_gb * 1e9) - resident
+    if budget <= 0:
+        raise SystemExit(f"resident state ({resident / 1e9:.1f} GB) exceeds the cap")
     warm = mixed_requests(200.0, 0.2, args.seed + 1, log_ns)
-    run_open_loop(Scheduler(be, int(args.cap_gb * 1e9), args.max_batch), warm)
+    run_open_loop(Scheduler(be, budget, args.max_batch), warm)
     reqs = mixed_requests(args.rate, args.seconds, args.seed, log_ns)
-    sched = Scheduler(be, int(args.cap_gb * 1e9), args.max_batch)
+    sched = Scheduler(be, budget, args.max_batch)
     wall = run_open_loop(sched, reqs, timeout=args.seconds * 20 + 120)
     stats = latency_stats(sched.completed)
     sizes = {}
@@ -318,7 +347,9 @@ def main():
                       "completed": len(sched.completed), "wall_s": round(wall, 3),
                       "sustained_ctmults_s": round(len(sched.completed) / wall, 1), "latency": stats,
                       "batches": sched.admitted_batches, "mean_batch": round(len(reqs) / max(1, sched.admitted_batches), 2),
-                      "streams": args.streams, "max_batch": args.max_batch, "cap_gb": args.cap_gb}))
+                      "streams": args.streams, "max_batch": args.max_batch, "cap_gb": args.cap_gb,
+                      "resident_gb": round(resident / 1e9, 2), "peak_allocated_gb": round(
+                          __import__("torch").cuda.max_memory_allocated() / 1e9, 2)}))
 
 
 if __name__ == "__main__":

@@ -67,7 +67,7 @@ def test_serving_mix_equals_alone(state):
     contexts, pools = state
     reqs = mixed_requests(400.0, 0.15, 11, log_ns=(10, 11), L=8, pool_size=24, k_range=(2, 6))
     assert len(reqs) > 20
-    be = GpuBackend(contexts, pools, n_streams=4)
+    be = GpuBackend(contexts, pools, n_streams=4, ws_bytes=256 << 20, keep_results=True)
     sched = Scheduler(be, cap_bytes=int(8e9), max_batch=4)
     run_open_loop(sched, reqs, timeout=120)
     assert len(sched.completed) == len(reqs)

@@ -73,6 +73,18 @@ def test_continuous_batching_admits_late_arrivals_while_running():
     assert {r.rid for r in s.completed} == {0, 1, 2}
 
 
+def test_batch_shrinks_to_the_backend_workspace():
+    class Small(FakeBackend):
+        def fits(self, shape, n):
+            return n <= 2
+    be = Small(n_streams=1)
+    s = Scheduler(be, cap_bytes=10 ** 9, max_batch=8)
+    for i in range(5):
+        s.submit(req(i))
+    s.step(0.0)
+    assert [len(b.reqs) for b in be.launched] == [2]
+
+
 def test_queue_limit_rejects():
     s = Scheduler(FakeBackend(), cap_bytes=10 ** 9, max_queue=2)
     assert s.submit(req(0)) and s.submit(req(1))
