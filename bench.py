@@ -50,6 +50,17 @@ CONFIG = {
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "traffic.json")
 
 
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Largest value over the ranks (the slowest rank's time); identity for
+    one rank. Works with any initialised process group (nccl or gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -230,11 +241,7 @@ def run_ours(args, rank, world, local_rank):
     ctx.check()
     for k, e0, e1 in all_evs:
         lat[k].append(e0.elapsed_time(e1))
-    ms_step = ms_total / args.steps
-    if world > 1:
-        tt = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = reduce_max(ms_total / args.steps, world, dev)
     products = B * len(ks) * world
     value = products / (ms_step / 1e3)
 
@@ -417,6 +424,7 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    ms = reduce_max(ms, world, dev)
     # upload bandwidth alone, for context
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(copy)
@@ -426,10 +434,6 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
                 dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
     t1.record(copy)
     t1.synchronize()
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
     ctx.check()
     return {"value": round(B * len(ks) * world / (ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),

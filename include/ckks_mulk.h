@@ -129,6 +129,21 @@ void ckks_plan_destroy(ckks_plan *plan);
  * rs_units = Table II's rescale-unit count below the root. */
 int ckks_plan_describe(const ckks_plan *plan, uint32_t *depth, uint32_t *rs_units, uint32_t *n_nodes);
 
+/* Partition search (Section V-C: among the partitions that keep the depth at
+ * ceil(log2 k), find the one of lowest complexity). Every valid tree for
+ * k inputs (2 <= k <= 12) is enumerated and costed by `criterion`:
+ * 0 = Table II's rescale-unit count; 1 = limb (I)NTTs of the whole k-input
+ * multiply at input `level` with K special primes and digits of `alpha`
+ * primes (Algorithm 1 at inner nodes, relinearisation and relocated rescale
+ * at the root). The cheapest tree's text (layered notation, NUL-terminated)
+ * is written to `text` (text_len bytes) and its cost to *cost; ties go to
+ * fewer nodes, then the smaller text. The text is parsed back before it is
+ * returned, so ckks_plan_create accepts it. ckks_plan_cost gives the same
+ * cost for an existing plan. Host only: no device work. */
+int ckks_plan_optimize(uint32_t k, int criterion, uint32_t level, uint32_t K, uint32_t alpha, char *text,
+                       size_t text_len, double *cost);
+int ckks_plan_cost(const ckks_plan *plan, int criterion, uint32_t level, uint32_t K, uint32_t alpha, double *cost);
+
 /* Workspace bytes for ckks_mul_k / ckks_mul_k_batch at this input level and
  * batch size. CKKS_ELEVEL if level <= depth or level > L. */
 int ckks_workspace_size(const ckks_context *ctx, const ckks_plan *plan, uint32_t level, uint32_t batch,
@@ -234,12 +249,20 @@ typedef struct {
 int ckks_profile_enable(ckks_context *ctx, int enable);
 int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, uint32_t *n_out);
 
-/* Launch tunables of a context (chosen by the autotuner; results are the
- * same for every value). Keys: "ntt_tile" = elements per NTT tile
- * (1024..8192, power of two; default 4096), "bconv_threads" = threads per
- * BConv block (64..1024, multiple of 32; default 256), "mac_threads" =
- * threads per key-MAC block (same range). CKKS_EINVAL for an unknown key or
- * an out-of-range value. */
+/* Launch tunables of a context; results are the same for every value.
+ * Chosen by the autotuner: "ntt_tile" = elements per NTT tile (1024..8192,
+ * power of two; default 4096), "bconv_threads" = threads per BConv block
+ * (64..1024, multiple of 32; default 256), "mac_threads" = threads per
+ * key-MAC block (same range).
+ * Forms of the rescaling, for measuring the paper's reformulations (every
+ * form gives the same residues): "inner_rescale" 0 = Algorithm 1 (mu INTT
+ * + (l - mu) NTT per polynomial, default), 1 = mu single rescales of Eq. 7,
+ * 2 = INTT of every limb, mu rescales of Eq. 6, NTT of the survivors (Table
+ * IV's baseline: l INTT + (l - mu) NTT); "root_rescale" 0 = relocated
+ * (Section IV: merged ModDown INTT, coefficient-domain rs, one NTT;
+ * default), 1 = prior (ModDown finished in the NTT domain, then the root's
+ * rescales by Eq. 7). CKKS_EINVAL for an unknown key or a value out of
+ * range. */
 int ckks_tune_set(ckks_context *ctx, const char *key, int value);
 int ckks_tune_get(const ckks_context *ctx, const char *key, int *value);
 

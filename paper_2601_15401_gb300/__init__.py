@@ -14,7 +14,7 @@ from dataclasses import dataclass
 
 from ._lib import ERRORS, CkksError, lib, library_path
 
-__all__ = ["Context", "Tuple", "CkksError", "library_path", "lib", "TABLE_II"]
+__all__ = ["Context", "Tuple", "CkksError", "library_path", "lib", "TABLE_II", "plan_optimize"]
 
 TABLE_II = {
     2: "(1,1)", 3: "(1,1,1)", 4: "(2,2)", 5: "(2,2,1)", 6: "(3,3)", 7: "(4,3)|(2,2)",
@@ -150,6 +150,19 @@ class Context:
         _check(lib().ckks_plan_describe(self.plan(k, partition), ctypes.byref(d), ctypes.byref(r), ctypes.byref(n)),
                "ckks_plan_describe")
         return {"depth": d.value, "rs_units": r.value, "nodes": n.value}
+
+    def plan_optimize(self, k: int, criterion: str = "transforms", level: int | None = None):
+        """Cheapest valid partition of k inputs: criterion "rs_units" (Table
+        II's count) or "transforms" (limb (I)NTTs at `level`, default L)."""
+        return plan_optimize(k, criterion, level if level is not None else self.L, self.K, self.alpha)
+
+    def plan_cost(self, k: int, partition: str | None = None, criterion: str = "transforms",
+                  level: int | None = None) -> float:
+        v = ctypes.c_double()
+        crit = 0 if criterion == "rs_units" else 1
+        _check(lib().ckks_plan_cost(self.plan(k, partition), crit, level if level is not None else self.L, self.K,
+                                    self.alpha, ctypes.byref(v)), "ckks_plan_cost")
+        return v.value
 
     def workspace_size(self, k: int, level: int, batch: int = 1, partition: str | None = None) -> int:
         n = ctypes.c_size_t()
@@ -296,6 +309,15 @@ class Context:
         _check(lib().ckks_profile_read(self._h, arr, 16, ctypes.byref(n)), "ckks_profile_read")
         return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms,
                                        "alg_bytes": arr[i].alg_bytes} for i in range(n.value)}
+
+
+def plan_optimize(k: int, criterion: str = "rs_units", level: int = 0, K: int = 0, alpha: int = 0):
+    """(partition text, cost) of the cheapest valid tree; host only."""
+    buf = ctypes.create_string_buffer(256)
+    v = ctypes.c_double()
+    crit = 0 if criterion == "rs_units" else 1
+    _check(lib().ckks_plan_optimize(k, crit, level, K, alpha, buf, 256, ctypes.byref(v)), "ckks_plan_optimize")
+    return buf.value.decode(), v.value
 
 
 class EvkSet:

@@ -35,6 +35,8 @@ SIGNATURES = {
     "ckks_plan_create": [V, U32, ctypes.c_char_p, V],
     "ckks_plan_destroy": [V],
     "ckks_plan_describe": [V, V, V, V],
+    "ckks_plan_optimize": [U32, I, U32, U32, U32, ctypes.c_char_p, SZ, V],
+    "ckks_plan_cost": [V, I, U32, U32, U32, V],
     "ckks_workspace_size": [V, V, U32, U32, V],
     "ckks_mul_k": [V, V, U32, V, V, V, V, SZ, V],
     "ckks_mul_k_batch": [V, V, U32, U32, V, V, V, V, SZ, V],

@@ -172,6 +172,27 @@ int ckks_plan_describe(const ckks_plan *plan, uint32_t *depth, uint32_t *rs_unit
     return CKKS_OK;
 }
 
+int ckks_plan_optimize(uint32_t k, int criterion, uint32_t level, uint32_t K, uint32_t alpha, char *text,
+                       size_t text_len, double *cost) {
+    if (!text || text_len == 0 || (criterion != 0 && criterion != 1) || (criterion == 1 && alpha == 0))
+        return CKKS_EINVAL;
+    std::string best;
+    double c = 0;
+    int rc = plan_optimize((int)k, criterion, (int)level, (int)K, (int)alpha, best, c);
+    if (rc == -2) return CKKS_ELEVEL;
+    if (rc != 0 || best.size() + 1 > text_len) return CKKS_EINVAL;
+    memcpy(text, best.c_str(), best.size() + 1);
+    if (cost) *cost = c;
+    return CKKS_OK;
+}
+
+int ckks_plan_cost(const ckks_plan *plan, int criterion, uint32_t level, uint32_t K, uint32_t alpha, double *cost) {
+    if (!plan || !cost || (criterion != 0 && criterion != 1) || (criterion == 1 && alpha == 0)) return CKKS_EINVAL;
+    if (criterion == 1 && (int)level <= plan->p.depth) return CKKS_ELEVEL;
+    *cost = plan_cost(plan->p, criterion, (int)level, (int)K, (int)alpha);
+    return CKKS_OK;
+}
+
 int ckks_workspace_size(const ckks_context *ctx, const ckks_plan *plan, uint32_t level, uint32_t batch,
                         size_t *bytes) {
     if (!ctx || !plan || !bytes || batch < 1) return CKKS_EINVAL;
@@ -491,6 +512,8 @@ static int *tune_slot(ckks_context *ctx, const char *key, int &lo, int &hi) {
     if (!strcmp(key, "ntt_tile")) { lo = 1024; hi = 8192; return &ctx->c.tune_ntt_tile; }
     if (!strcmp(key, "bconv_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_bconv_threads; }
     if (!strcmp(key, "mac_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_mac_threads; }
+    if (!strcmp(key, "inner_rescale")) { lo = 0; hi = 2; return &ctx->c.tune_inner_rescale; }
+    if (!strcmp(key, "root_rescale")) { lo = 0; hi = 1; return &ctx->c.tune_root_rescale; }
     return nullptr;
 }
 
@@ -499,7 +522,7 @@ int ckks_tune_set(ckks_context *ctx, const char *key, int value) {
     int *slot = tune_slot(ctx, key, lo, hi);
     if (!slot || value < lo || value > hi) return CKKS_EINVAL;
     if (!strcmp(key, "ntt_tile") && (value & (value - 1))) return CKKS_EINVAL;
-    if (strcmp(key, "ntt_tile") && value % 32) return CKKS_EINVAL;
+    if ((!strcmp(key, "bconv_threads") || !strcmp(key, "mac_threads")) && value % 32) return CKKS_EINVAL;
     *slot = value;
     return CKKS_OK;
 }

@@ -107,8 +107,8 @@ cudaError_t transform_plain(const Context &C, bool fwd, int B, int polys, int le
 }
 
 // Algorithm 1 on `polys` polynomials: in (level limbs, NTT) -> out (level - mu).
-cudaError_t multi_rs(const Context &C, Ws &ws, int B, int polys, int level, int mu, LimbView in, LimbView out,
-                     cudaStream_t st) {
+static cudaError_t multi_rs_alg1(const Context &C, Ws &ws, int B, int polys, int level, int mu, LimbView in,
+                                 LimbView out, cudaStream_t st) {
     const int N = C.N;
     u64 *a = ws.take((size_t)B * polys * mu * N);
     u64 *bb = ws.take((size_t)B * polys * (level - mu) * N);
@@ -168,6 +168,59 @@ cudaError_t multi_rs(const Context &C, Ws &ws, int B, int polys, int level, int 
         TRY(ntt_transform(C, true, J, L, S, &mid, st));
     }
     return cudaSuccess;
+}
+
+static cudaError_t root_rescale(const Context &C, int B, int level, int mu, LimbView cstar, LimbView out,
+                                cudaStream_t st);
+
+// Rescaling of a tuple by mu primes in the NTT domain, in the form the
+// context's "inner_rescale" setting selects (all forms give the same
+// residues, Section V-B):
+//   0  Algorithm 1: mu INTT + (level - mu) NTT per polynomial;
+//   1  mu single rescales of Eq. 7, one after the other;
+//   2  INTT of every limb, the mu rescales of Eq. 6 in the coefficient
+//      domain (combined as in Eq. 17), NTT of the survivors: level INTT +
+//      (level - mu) NTT per polynomial (Table IV's baseline).
+cudaError_t multi_rs(const Context &C, Ws &ws, int B, int polys, int level, int mu, LimbView in, LimbView out,
+                     cudaStream_t st) {
+    if (C.tune_inner_rescale == 1 && mu > 1) {
+        TRY(multi_rs_alg1(C, ws, B, polys, level, 1, in, out, st));
+        for (int j = 1; j < mu; ++j) TRY(multi_rs_alg1(C, ws, B, polys, level - j, 1, out, out, st));
+        return cudaSuccess;
+    }
+    if (C.tune_inner_rescale == 2) {
+        const int N = C.N;
+        u64 *a = ws.take((size_t)B * polys * level * N);
+        if (ws.dry) return cudaSuccess;
+        LimbView av = view(a, (i64)polys * level * N, (i64)level * N);
+        TRY(transform_plain(C, false, B, polys, level, in, av, st));
+        LimbView top = offset(av, (i64)(level - mu) * N);
+        RsChainArgs R;
+        R.n_batch = B;
+        R.n_polys = polys;
+        R.N = N;
+        R.level = level;
+        R.mu = mu;
+        R.v = top;
+        R.mods = C.d_mods;
+        R.one = C.d_one;
+        R.invq = C.d_invq;
+        TRY(launch_rschain(C, R, st));
+        LimbJobs J = jobs(B, polys, level - mu);
+        const Shoup *g = C.d_g + C.g_off[level][mu];
+        LoadSpec L{};
+        L.mode = LD_EQ17;
+        L.a = av;
+        L.b = top;
+        L.g = g;
+        L.mu = mu;
+        L.with_self = 1;
+        StoreSpec S{};
+        S.mode = ST_REDUCE;
+        S.dst = out;
+        return ntt_transform(C, true, J, L, S, nullptr, st);
+    }
+    return multi_rs_alg1(C, ws, B, polys, level, mu, in, out, st);
 }
 
 // Relinearisation up to the coefficient-domain c* (or the NTT-domain C* of
@@ -395,11 +448,24 @@ int run_mul_k(const Context &C, const Plan &P, int level, int B, const LimbView 
             if (n > t_max) return -3;
             u64 *cs = ws.take((size_t)B * 2 * lv * N);
             LimbView cv = view(cs, (i64)2 * lv * N, (i64)lv * N);
-            err = relin_core(C, ws, B, n, lv, dv, keys, t_max, false, cv, st);
-            if (err != cudaSuccess) return -5;
-            if (!ws.dry) {
-                err = root_rescale(C, B, lv, nd.mu, cv, out, st);
+            if (C.tune_root_rescale == 1) {
+                // prior arrangement: ModDown finished in the NTT domain, then
+                // mu_root rescales of Eq. 7
+                err = relin_core(C, ws, B, n, lv, dv, keys, t_max, true, cv, st);
                 if (err != cudaSuccess) return -5;
+                err = multi_rs_alg1(C, ws, B, 2, lv, 1, cv, nd.mu == 1 ? out : cv, st);
+                if (err != cudaSuccess) return -5;
+                for (int j = 1; j < nd.mu; ++j) {
+                    err = multi_rs_alg1(C, ws, B, 2, lv - j, 1, cv, j == nd.mu - 1 ? out : cv, st);
+                    if (err != cudaSuccess) return -5;
+                }
+            } else {
+                err = relin_core(C, ws, B, n, lv, dv, keys, t_max, false, cv, st);
+                if (err != cudaSuccess) return -5;
+                if (!ws.dry) {
+                    err = root_rescale(C, B, lv, nd.mu, cv, out, st);
+                    if (err != cudaSuccess) return -5;
+                }
             }
         }
     }

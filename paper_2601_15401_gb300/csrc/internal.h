@@ -121,6 +121,10 @@ struct Context {
     int tune_ntt_tile = 4096;
     int tune_bconv_threads = 256;
     int tune_mac_threads = 256;
+    // forms of the rescaling (same results; for measuring the paper's
+    // reformulations): see multi_rs and run_mul_k in engine.cu
+    int tune_inner_rescale = 0;
+    int tune_root_rescale = 0;
 };
 
 // Records CUDA events around one launch on its stream when the hook is on;

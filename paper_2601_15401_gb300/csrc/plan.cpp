@@ -10,7 +10,9 @@
 // sum of rescales on a leaf-to-root path; valid iff depth <= ceil(log2 k).
 #include "plan.h"
 
+#include <algorithm>
 #include <cctype>
+#include <cmath>
 #include <cstring>
 
 namespace ckks {
@@ -182,6 +184,171 @@ void plan_levels(const Plan &P, int level, std::vector<int> &lvl_in, std::vector
         lvl_out[i] = lmin - P.nodes[i].mu;
         polys[i] = P.nodes[i].root ? 2 : p;
     }
+}
+
+}  // namespace ckks
+
+namespace ckks {
+
+// ---------------------------------------------------------------------------
+// Partition search (Section V-C asks for the partition of lowest complexity
+// among those that keep the depth at ceil(log2 k)). Every valid tree is
+// enumerated; each is costed by one criterion:
+//   kCostRsUnits   Table II's count: size + 1 rescale units per non-root node;
+//   kCostTransforms limb (I)NTTs of the whole k-input multiply at an input
+//                  level (Algorithm 1 at inner nodes: level per polynomial;
+//                  the root's relinearisation and relocated rescale).
+// The text of the cheapest tree in the layered notation is parsed back and
+// re-costed, so the returned partition is exactly the tree that was costed.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TNode {
+    int size;
+    std::vector<TNode> kids;  // empty: a leaf (size 1) or an undivided group
+    int depth() const {
+        if (kids.empty()) return size >= 2 ? size - 1 : 0;
+        int d = 0;
+        for (auto &k : kids) d = std::max(d, k.depth());
+        return (int)kids.size() - 1 + d;
+    }
+};
+
+// all sub-trees over g inputs with depth <= budget
+void subtrees(int g, int budget, std::vector<TNode> &out);
+
+void split_into(int remaining, int maxpart, std::vector<int> &parts, std::vector<std::vector<int>> &all) {
+    if (remaining == 0) {
+        all.push_back(parts);
+        return;
+    }
+    for (int p = std::min(remaining, maxpart); p >= 1; --p) {
+        parts.push_back(p);
+        split_into(remaining - p, p, parts, all);
+        parts.pop_back();
+    }
+}
+
+void combine(const std::vector<int> &parts, size_t i, int budget, std::vector<TNode> &cur, std::vector<TNode> &out,
+             int g) {
+    if (i == parts.size()) {
+        TNode n{g, cur};
+        out.push_back(n);
+        return;
+    }
+    std::vector<TNode> opts;
+    subtrees(parts[i], budget, opts);
+    for (auto &o : opts) {
+        cur.push_back(o);
+        combine(parts, i + 1, budget, cur, out, g);
+        cur.pop_back();
+    }
+}
+
+void subtrees(int g, int budget, std::vector<TNode> &out) {
+    if (g == 1) {
+        out.push_back(TNode{1, {}});
+        return;
+    }
+    if (g - 1 <= budget) out.push_back(TNode{g, {}});  // undivided: g inputs, g - 1 rescales
+    std::vector<std::vector<int>> all;
+    std::vector<int> parts;
+    split_into(g, g, parts, all);
+    for (auto &ps : all) {
+        const int m = (int)ps.size();
+        if (m < 2 || m - 1 > budget) continue;
+        bool all_ones = true;
+        for (int p : ps) all_ones = all_ones && p == 1;
+        if (all_ones) continue;  // same tree as the undivided group
+        std::vector<TNode> cur;
+        combine(ps, 0, budget - (m - 1), cur, out, g);
+    }
+}
+
+// layered text; children ordered by size (desc), divided before undivided
+std::string layered_text(const TNode &root) {
+    std::string text;
+    std::vector<const TNode *> layer{&root};
+    bool first = true;
+    while (!layer.empty()) {
+        std::vector<const TNode *> next;
+        std::string groups;
+        for (const TNode *n : layer) {
+            if (n->kids.empty()) continue;
+            std::vector<const TNode *> kids;
+            for (auto &k : n->kids) kids.push_back(&k);
+            std::stable_sort(kids.begin(), kids.end(), [](const TNode *a, const TNode *b) {
+                if (a->size != b->size) return a->size > b->size;
+                return !a->kids.empty() && b->kids.empty();
+            });
+            groups += "(";
+            for (size_t i = 0; i < kids.size(); ++i) groups += (i ? "," : "") + std::to_string(kids[i]->size);
+            groups += "),";
+            for (auto *k : kids) next.push_back(k);
+        }
+        if (groups.empty()) break;
+        groups.pop_back();
+        text += (first ? "" : "|") + groups;
+        first = false;
+        layer = next;
+    }
+    return text;
+}
+
+}  // namespace
+
+double plan_cost(const Plan &P, int criterion, int level, int K, int alpha) {
+    if (criterion == kCostRsUnits) return P.rs_units;
+    std::vector<int> lin, lout, polys;
+    plan_levels(P, level, lin, lout, polys);
+    double c = 0;
+    for (size_t i = 0; i < P.nodes.size(); ++i) {
+        const PlanNode &n = P.nodes[i];
+        if (!n.root) {
+            c += (double)(n.size + 1) * lin[i];  // Algorithm 1: l transforms per polynomial
+        } else {
+            const int l = lin[i], nn = P.k, mu = n.mu;
+            const int digits = (l + alpha - 1) / alpha;
+            double modup = 0;
+            for (int b = 0; b < digits; ++b) modup += l + K - std::min(alpha, l - b * alpha);
+            c += (nn - 1) * l + (nn - 1) * modup + 2.0 * K + 2.0 * l + 2.0 * (l - mu);
+        }
+    }
+    return c;
+}
+
+int plan_optimize(int k, int criterion, int level, int K, int alpha, std::string &best_text, double &best_cost) {
+    if (k < 2 || k > 12) return -1;
+    const int D = ceil_log2(k);
+    if (criterion == kCostTransforms && level <= D) return -2;
+    std::vector<TNode> roots;
+    std::vector<std::vector<int>> all;
+    std::vector<int> parts;
+    split_into(k, k, parts, all);
+    for (auto &ps : all) {
+        const int m = (int)ps.size();
+        if (m < 2 || m - 1 > D) continue;
+        std::vector<TNode> cur;
+        combine(ps, 0, D - (m - 1), cur, roots, k);
+    }
+    best_cost = 1e300;
+    best_text.clear();
+    size_t best_nodes = 0;
+    for (auto &r : roots) {
+        std::string t = layered_text(r);
+        Plan P;
+        if (plan_build(P, k, t.c_str()) != 0) continue;  // the text must parse back to a valid tree
+        double c = plan_cost(P, criterion, level, K, alpha);
+        const bool better = c < best_cost - 1e-9 ||
+                            (std::fabs(c - best_cost) < 1e-9 &&
+                             (P.nodes.size() < best_nodes || (P.nodes.size() == best_nodes && t < best_text)));
+        if (better) {
+            best_cost = c;
+            best_text = t;
+            best_nodes = P.nodes.size();
+        }
+    }
+    return best_text.empty() ? -1 : 0;
 }
 
 }  // namespace ckks

@@ -26,10 +26,14 @@ def main():
     ap.add_argument("--k", type=int, default=8)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--tune", action="append", default=[], help="key=value library tunable")
     args = ap.parse_args()
     p = synth.params_large(log_n=args.log_n)
     ctx = G.Context.from_params(p)
     L, N, B = p.L, p.N, args.batch
+    for kv in args.tune:
+        key, val = kv.split("=")
+        ctx.tune_set(key, int(val))
     if args.op == "ntt":
         x = synth.uniform_residues_torch(p.q, (B * 2,), N, 7, "cuda")  # [2B][L][N]
         T = G.Tuple(x, 2 * B, L, L, 0)
@@ -73,6 +77,7 @@ def main():
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize()
+    ctx.counters(reset=True)
     ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -84,7 +89,8 @@ def main():
     prof = ctx.profile_read()
     ctx.check()
     print(json.dumps({
-        "op": args.op, "log_n": args.log_n, "batch": B, "k": args.k, "ms_per_rep": round(e0.elapsed_time(e1) / args.reps, 4),
+        "op": args.op, "log_n": args.log_n, "batch": B, "k": args.k, "tune": args.tune,
+        "ms_per_rep": round(e0.elapsed_time(e1) / args.reps, 4), "counters_per_rep": {n: v // args.reps for n, v in ctx.counters().items()},
         "kernels": {n: {"launches": v["launches"], "avg_us": round(v["total_ms"] * 1e3 / v["launches"], 2),
                         "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)} for n, v in prof.items()}}))
 

@@ -66,3 +66,46 @@ def test_plan_rejections(L):
     assert _describe(L, 4, "(1,1,1,1)")[0] == -1        # depth 3 > 2
     assert _describe(L, 5, "(2,2)")[0] == -1            # sizes do not add up
     assert _describe(L, 7, "(4,3)|(2,1)")[0] == -1      # no group of 3 split (2,1)? it is valid
+
+
+@pytest.mark.parametrize("k", range(2, 13))
+def test_partition_search_reaches_table_ii_minimum(L, k):
+    import paper_2601_15401_gb300 as G
+    text, cost = G.plan_optimize(k, "rs_units")
+    root = oplan.parse(text, k)
+    assert oplan.valid(root, k)
+    assert cost == oplan.rs_units(root) == oplan.min_rs_units(k)
+
+
+def test_transform_cost_matches_table_v_total():
+    """Table V: the improved 3-input multiply at dnum = 1, K = L performs
+    2L + 2K - 4 NTT and 4L + 2K INTT limb transforms."""
+    import ctypes
+
+    import paper_2601_15401_gb300 as G
+    from paper_2601_15401_gb300._lib import lib
+    for Lq in (4, 12, 24):
+        h = ctypes.c_void_p()
+        assert lib().ckks_plan_create(None, 3, b"(1,1,1)", ctypes.byref(h)) == 0
+        c = ctypes.c_double()
+        assert lib().ckks_plan_cost(h, 1, Lq, Lq, Lq, ctypes.byref(c)) == 0
+        lib().ckks_plan_destroy(h)
+        assert c.value == (2 * Lq + 2 * Lq - 4) + (4 * Lq + 2 * Lq)
+    text, cost = G.plan_optimize(3, "transforms", 24, 24, 24)
+    assert text == "(1,1,1)" and cost == 6 * 24 + 4 * 24 - 4
+
+
+def test_transform_search_beats_or_ties_every_table_ii_tree(L):
+    import ctypes
+
+    import paper_2601_15401_gb300 as G
+    from paper_2601_15401_gb300._lib import lib
+    for k in range(2, 13):
+        best_text, best = G.plan_optimize(k, "transforms", 24, 8, 8)
+        h = ctypes.c_void_p()
+        assert lib().ckks_plan_create(None, k, None, ctypes.byref(h)) == 0
+        c = ctypes.c_double()
+        assert lib().ckks_plan_cost(h, 1, 24, 8, 8, ctypes.byref(c)) == 0
+        lib().ckks_plan_destroy(h)
+        assert best <= c.value
+        assert oplan.valid(oplan.parse(best_text, k), k)

@@ -252,3 +252,40 @@ def test_error_codes(S12):
         S12.ctx.mul_k(tups, S12.evk, out, S12.ws(need))
     assert e.value.code == -1
     S12.ctx.check()
+
+
+# ---------------------------------------------------------------------------
+# forms of the rescaling (same residues; Section IV and V-B)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("key,value", [("inner_rescale", 1), ("inner_rescale", 2), ("root_rescale", 1)])
+@pytest.mark.parametrize("k", [3, 7, 9])
+def test_rescale_forms_give_identical_products(S12, key, value, k):
+    level = 7 if k > 8 else 6
+    cts = _inputs(S12, k, level, 213, 10 * k)
+    base = host(_run_mul_k(S12, cts, level).data)
+    S12.ctx.tune_set(key, value)
+    try:
+        other = host(_run_mul_k(S12, cts, level).data)
+    finally:
+        S12.ctx.tune_set(key, 0)
+    assert np.array_equal(other, base)
+
+
+def test_table_iv_counts_for_each_rescale_form():
+    """Table IV: mu combined rescales cost mu INTT + (L - mu) NTT per
+    polynomial (Algorithm 1); the baseline costs L INTT + (L - mu) NTT."""
+    import paper_2601_15401_gb300 as G
+    params = synth.make_params(5, [50] * 8, 2, 2)
+    ctx = G.Context.from_params(params)
+    L = 8
+    t = G.Tuple.wrap(dev(np.stack([synth.uniform_residues(synth.rng(2), params.q, params.N)])))
+    for mode, want in [(0, lambda mu: (mu, L - mu)), (2, lambda mu: (L, L - mu)),
+                       (1, lambda mu: (mu, sum(L - 1 - j for j in range(mu))))]:
+        ctx.tune_set("inner_rescale", mode)
+        for mu in (1, 3):
+            ws = dev(np.zeros(ctx.rescale_workspace_size(1, L, mu) // 8 + 1, dtype=np.uint64))
+            ctx.counters(reset=True)
+            ctx.rescale_multi(t, mu, G.Tuple.wrap(dev(np.zeros((1, L - mu, params.N), dtype=np.uint64))), ws)
+            c = ctx.counters(reset=True)
+            assert (c["limb_intt"], c["limb_ntt"]) == want(mu), (mode, mu)
+    ctx.tune_set("inner_rescale", 0)
