@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--tune", action="append", default=[], help="key=value library tunable")
+    ap.add_argument("--partition", default=None, help="partition text for --op mul_k (default Table II)")
     args = ap.parse_args()
     p = synth.params_large(log_n=args.log_n)
     ctx = G.Context.from_params(p)
@@ -55,15 +56,15 @@ def main():
         evk = ctx.evk_set(t_max, keys)
         if args.op == "mul_k":
             k = args.k
-            depth = ctx.plan_describe(k)["depth"]
+            depth = ctx.plan_describe(k, args.partition)["depth"]
             inp = synth.uniform_residues_torch(p.q, (B, k, 2), N, 11, "cuda")
             out = torch.empty((B, 2, L - depth, N), dtype=torch.uint64, device="cuda")
             tup = [[G.Tuple(inp[b, u], 2, L, L) for u in range(k)] for b in range(B)]
             outs = [G.Tuple(out[b], 2, L - depth, L - depth) for b in range(B)]
-            ws = torch.empty(ctx.workspace_size(k, L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
+            ws = torch.empty(ctx.workspace_size(k, L, B, args.partition) // 8 + 1, dtype=torch.uint64, device="cuda")
 
             def run():
-                ctx.mul_k_batch(tup, evk, outs, ws)
+                ctx.mul_k_batch(tup, evk, outs, ws, partition=args.partition)
         else:
             inp = synth.uniform_residues_torch(p.q, (B, 2, 2), N, 12, "cuda")
             out = torch.empty((B, 2, L - 1, N), dtype=torch.uint64, device="cuda")
@@ -89,7 +90,7 @@ def main():
     prof = ctx.profile_read()
     ctx.check()
     print(json.dumps({
-        "op": args.op, "log_n": args.log_n, "batch": B, "k": args.k, "tune": args.tune,
+        "op": args.op, "log_n": args.log_n, "batch": B, "k": args.k, "tune": args.tune, "partition": args.partition,
         "ms_per_rep": round(e0.elapsed_time(e1) / args.reps, 4), "counters_per_rep": {n: v // args.reps for n, v in ctx.counters().items()},
         "kernels": {n: {"launches": v["launches"], "avg_us": round(v["total_ms"] * 1e3 / v["launches"], 2),
                         "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)} for n, v in prof.items()}}))

@@ -289,3 +289,25 @@ def test_table_iv_counts_for_each_rescale_form():
             c = ctx.counters(reset=True)
             assert (c["limb_intt"], c["limb_ntt"]) == want(mu), (mode, mu)
     ctx.tune_set("inner_rescale", 0)
+
+
+@pytest.mark.parametrize("log_n,k", [(9, 5), (11, 7), (13, 4), (15, 3)])
+def test_mul_k_parity_two_phase_geometries(log_n, k):
+    """Ring degrees whose transforms split unevenly (N1 != N2) and the
+    serving mix's degrees, against the oracle."""
+    S = _setup(log_n, 5, 2, 2, k, 214 + log_n)
+    level = 5
+    cts = _inputs(S, k, level, 214, 100 * log_n)
+    out = _run_mul_k(S, cts, level)
+    want = O.mul_k(S.octx, [oracle_tuple(c) for c in cts], S.okeys)
+    assert np.array_equal(host(out.data)[:, :out.level], want.data)
+
+
+def test_mul_k_k10_search_partition_matches_oracle(S12):
+    """The partition the transform-count search prefers for k = 10."""
+    import paper_2601_15401_gb300 as G
+    part, _ = G.plan_optimize(10, "transforms", 24, 8, 8)
+    cts = _inputs(S12, 10, 7, 215)
+    out = _run_mul_k(S12, cts, 7, part)
+    want = O.mul_k(S12.octx, [oracle_tuple(c) for c in cts], S12.okeys, part)
+    assert np.array_equal(host(out.data)[:, :out.level], want.data)
