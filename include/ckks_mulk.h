@@ -116,6 +116,26 @@ int ckks_keygen_evk(ckks_context *ctx, uint32_t t_max, const int64_t *s, const u
 int ckks_evk_set_create(ckks_context *ctx, uint32_t t_max, uint64_t *keys, void *stream, ckks_evk_set **out);
 void ckks_evk_set_destroy(ckks_evk_set *set);
 
+/* ------------------------------------------------------ around the product
+ * Section II's public key, encryption and decryption, on the device.
+ * ckks_public_key: pk = (-a s + e, a) on the L Q limbs, NTT domain; s, e
+ * device int64 [N] (small), a device [L][N] residues (NTT domain), pk device
+ * [2][L][N]. ckks_encrypt: out = (v pk_0 + e_0 + m, v pk_1 + e_1) on limbs
+ * 0..level-1, NTT domain; m, v, e_0, e_1 device int64 [N] (|m| < 2^62: the
+ * integer message polynomial, e.g. scaled and rounded canonical-embedding
+ * coefficients). ckks_decrypt: c_0 + c_1 s on the lowest two limbs (one at
+ * level 1), lifted by CRT to [0, q_0 q_1) and centred, written as double
+ * [N] (device); exact while |message| < q_0 q_1 / 2. Workspace for all
+ * three: ckks_encrypt_workspace_size. */
+int ckks_encrypt_workspace_size(const ckks_context *ctx, size_t *bytes);
+int ckks_public_key(ckks_context *ctx, const int64_t *s, const uint64_t *a, const int64_t *e, uint64_t *pk,
+                    void *workspace, size_t ws_bytes, void *stream);
+int ckks_encrypt(ckks_context *ctx, const int64_t *m, const int64_t *v, const int64_t *e0, const int64_t *e1,
+                 const uint64_t *pk, uint32_t level, ckks_tuple *out, void *workspace, size_t ws_bytes,
+                 void *stream);
+int ckks_decrypt(ckks_context *ctx, const ckks_tuple *ct, const int64_t *s, double *out, void *workspace,
+                 size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------- plans
  * ckks_plan_create: the partition tree of a k-input multiply (2 <= k <= 12)
  * in the notation of Table II, e.g. "(4,3)|(2,2)": '|' separates layers and
@@ -255,14 +275,19 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
  * (64..1024, multiple of 32; default 256), "mac_threads" = threads per
  * key-MAC block (same range).
  * Forms of the rescaling, for measuring the paper's reformulations (every
- * form gives the same residues): "inner_rescale" 0 = Algorithm 1 (mu INTT
+ * rescaling form gives the same residues): "inner_rescale" 0 = Algorithm 1 (mu INTT
  * + (l - mu) NTT per polynomial, default), 1 = mu single rescales of Eq. 7,
  * 2 = INTT of every limb, mu rescales of Eq. 6, NTT of the survivors (Table
  * IV's baseline: l INTT + (l - mu) NTT); "root_rescale" 0 = relocated
  * (Section IV: merged ModDown INTT, coefficient-domain rs, one NTT;
  * default), 1 = prior (ModDown finished in the NTT domain, then the root's
- * rescales by Eq. 7). CKKS_EINVAL for an unknown key or a value out of
- * range. */
+ * rescales by Eq. 7). Form of the key switching (Section III): "moddown"
+ * 0 = the key products of every ek_t summed before one ModDown (Eq. 15,
+ * default), 1 = one ModDown per ek_t, the results summed (the form Eq. 15
+ * replaces; its residues differ from the combined form's by the same small
+ * integer W in [0, K (n - 2)] in every limb, the extra wraps of Eq. 5's
+ * P-residues; it needs no more workspace). CKKS_EINVAL for an unknown key
+ * or a value out of range. */
 int ckks_tune_set(ckks_context *ctx, const char *key, int value);
 int ckks_tune_get(const ckks_context *ctx, const char *key, int *value);
 

@@ -287,15 +287,15 @@ def keygen_all(ctx: Ctx, km, t_max: int):
 # ---------------------------------------------------------------------------
 # Eq. 15: relinearisation with one combined ModDown per output polynomial
 # ---------------------------------------------------------------------------
-def relin_accumulate(ctx: Ctx, d: np.ndarray, keys, level: int) -> np.ndarray:
+def relin_accumulate(ctx: Ctx, d: np.ndarray, keys, level: int, ts=None) -> np.ndarray:
     """acc_l = sum_{t >= 2} sum_beta ModUp_beta(d_t) * ek_{t,beta,l}
     (NTT domain, [2][level + K][N]) -- the sum taken before the single
-    ModDown (Section III, combined form)."""
+    ModDown (Section III, combined form). `ts` restricts the sum to some t."""
     n = d.shape[0] - 1
     kp = key_primes(ctx, level)
     rows = key_rows(ctx, level)
     acc = np.zeros((2, level + ctx.K, ctx.N), dtype=np.uint64)
-    for t in range(2, n + 1):
+    for t in (range(2, n + 1) if ts is None else ts):
         for beta, digit in enumerate(ctx.digits(level)):
             ext = modup(ctx, d[t], level, digit)
             for l in range(2):
@@ -304,29 +304,37 @@ def relin_accumulate(ctx: Ctx, d: np.ndarray, keys, level: int) -> np.ndarray:
     return acc
 
 
-def relin_coef(ctx: Ctx, d: np.ndarray, keys, level: int) -> np.ndarray:
+def _moddowns(ctx: Ctx, d: np.ndarray, keys, level: int, separate: bool) -> np.ndarray:
+    """ModDown (Eq. 5) of the key products, coefficient domain [2][level][N].
+    Combined (Eq. 15): one ModDown of the sum over t. Separate (the form the
+    paper replaces): one ModDown per ek_t, the results summed."""
+    n = d.shape[0] - 1
+    kp = key_primes(ctx, level)
+    qs = ctx.q[:level]
+    groups = [[t] for t in range(2, n + 1)] if separate else [None]
+    out = np.zeros((2, level, ctx.N), dtype=np.uint64)
+    for ts in groups:
+        acc = relin_accumulate(ctx, d, keys, level, ts)
+        for l in range(2):
+            out[l] = ring.addmod_rows(out[l], moddown_coef(ctx, intt_poly(acc[l], kp), level), qs)
+    return out
+
+
+def relin_coef(ctx: Ctx, d: np.ndarray, keys, level: int, separate: bool = False) -> np.ndarray:
     """c* = (d_0, d_1) + sum_t ceil(P^-1 d_t ek_t) in the coefficient domain
     ([2][level][N]): ModDown (Eq. 5) of the accumulated product, added to
     INTT(d_0), INTT(d_1)."""
-    acc = relin_accumulate(ctx, d, keys, level)
-    kp = key_primes(ctx, level)
-    out = np.empty((2, level, ctx.N), dtype=np.uint64)
-    for l in range(2):
-        c_hat = moddown_coef(ctx, intt_poly(acc[l], kp), level)
-        out[l] = ring.addmod_rows(intt_poly(d[l], ctx.q[:level]), c_hat, ctx.q[:level])
-    return out
+    c_hat = _moddowns(ctx, d, keys, level, separate)
+    qs = ctx.q[:level]
+    return np.stack([ring.addmod_rows(intt_poly(d[l], qs), c_hat[l], qs) for l in range(2)])
 
 
-def relin_ntt(ctx: Ctx, d: np.ndarray, keys, level: int) -> np.ndarray:
+def relin_ntt(ctx: Ctx, d: np.ndarray, keys, level: int, separate: bool = False) -> np.ndarray:
     """The same relinearisation in the prior (standard) arrangement: ModDown
     transformed back to the NTT domain and added to D_0, D_1 there."""
-    acc = relin_accumulate(ctx, d, keys, level)
-    kp = key_primes(ctx, level)
-    out = np.empty((2, level, ctx.N), dtype=np.uint64)
-    for l in range(2):
-        c_hat = moddown_coef(ctx, intt_poly(acc[l], kp), level)
-        out[l] = ring.addmod_rows(d[l], ntt_poly(c_hat, ctx.q[:level]), ctx.q[:level])
-    return out
+    c_hat = _moddowns(ctx, d, keys, level, separate)
+    qs = ctx.q[:level]
+    return np.stack([ring.addmod_rows(d[l], ntt_poly(c_hat[l], qs), qs) for l in range(2)])
 
 
 # ---------------------------------------------------------------------------
@@ -349,7 +357,7 @@ def align(children: list[Tup]) -> list[Tup]:
 
 
 def eval_node(ctx: Ctx, node: _plan.Node, leaves: list, keys, pos: list, root: bool,
-              rescale: str = "sequential") -> Tup:
+              rescale: str = "sequential", separate: bool = False) -> Tup:
     if node.is_leaf:
         ct = leaves[pos[0]]
         pos[0] += 1
@@ -360,7 +368,7 @@ def eval_node(ctx: Ctx, node: _plan.Node, leaves: list, keys, pos: list, root: b
     level = kids[0].level
     mu = len(node.children) - 1
     if root:
-        cstar = relin_coef(ctx, D, keys, level)
+        cstar = relin_coef(ctx, D, keys, level, separate)
         for _ in range(mu):
             cstar = np.stack([rs(ctx, cstar[l]) for l in range(2)])
         out_level = level - mu
@@ -374,17 +382,18 @@ def eval_node(ctx: Ctx, node: _plan.Node, leaves: list, keys, pos: list, root: b
 
 
 def mul_k(ctx: Ctx, cts: list[Tup], keys, partition: str | None = None,
-          rescale: str = "sequential") -> Tup:
+          rescale: str = "sequential", separate_moddown: bool = False) -> Tup:
     """k-input product: tensor products and multi-rescales at the inner nodes
     (bottom-up), relinearisation at the root (Eq. 15), then the root's
     m - 1 rescales in the coefficient domain and one NTT (relocated
-    rescale, Section IV)."""
+    rescale, Section IV). `separate_moddown` takes one ModDown per ek_t
+    instead of Eq. 15's single one."""
     k = len(cts)
     part = partition or _plan.TABLE_II[k]
     root = _plan.parse(part, k)
     if not _plan.valid(root, k):
         raise ValueError(f"partition {part} breaks the depth rule")
-    return eval_node(ctx, root, cts, keys, [0], True, rescale)
+    return eval_node(ctx, root, cts, keys, [0], True, rescale, separate_moddown)
 
 
 def mul2_standard(ctx: Ctx, a: Tup, b: Tup, keys) -> Tup:

@@ -129,6 +129,32 @@ class Context:
                                      workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                      _stream(stream)), "ckks_keygen_evk")
 
+    # ------------------------------------------------------- around the product
+    def encrypt_workspace_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ckks_encrypt_workspace_size(self._h, ctypes.byref(n)), "ckks_encrypt_workspace_size")
+        return n.value
+
+    def public_key(self, s, a, e, pk, workspace, stream=None):
+        _check(lib().ckks_public_key(self._h, s.data_ptr(), a.data_ptr(), e.data_ptr(), pk.data_ptr(),
+                                     workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                     _stream(stream)), "ckks_public_key")
+
+    def encrypt(self, m, v, e0, e1, pk, level: int, out: Tuple, workspace, stream=None) -> Tuple:
+        o = out.c()
+        _check(lib().ckks_encrypt(self._h, m.data_ptr(), v.data_ptr(), e0.data_ptr(), e1.data_ptr(), pk.data_ptr(),
+                                  level, ctypes.byref(o), workspace.data_ptr(),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)), "ckks_encrypt")
+        out.level, out.n_polys, out.ntt_form, out.poly_stride = o.level, o.n_polys, o.ntt_form, o.poly_stride
+        return out
+
+    def decrypt(self, ct: Tuple, s, out, workspace, stream=None):
+        """out: float64 CUDA tensor [N] <- centred c_0 + c_1 s (two lowest limbs)."""
+        c = ct.c()
+        _check(lib().ckks_decrypt(self._h, ctypes.byref(c), s.data_ptr(), out.data_ptr(), workspace.data_ptr(),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)), "ckks_decrypt")
+        return out
+
     def evk_set(self, t_max: int, keys, stream=None) -> "EvkSet":
         h = ctypes.c_void_p()
         _check(lib().ckks_evk_set_create(self._h, t_max, keys.data_ptr(), _stream(stream), ctypes.byref(h)),

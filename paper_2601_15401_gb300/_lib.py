@@ -31,6 +31,10 @@ SIGNATURES = {
     "ckks_keygen_workspace_size": [V, V],
     "ckks_keygen_evk": [V, U32, V, V, V, V, V, SZ, V],
     "ckks_evk_set_create": [V, U32, V, V, V],
+    "ckks_encrypt_workspace_size": [V, V],
+    "ckks_public_key": [V, V, V, V, V, V, SZ, V],
+    "ckks_encrypt": [V, V, V, V, V, V, U32, V, V, SZ, V],
+    "ckks_decrypt": [V, V, V, V, V, SZ, V],
     "ckks_evk_set_destroy": [V],
     "ckks_plan_create": [V, U32, ctypes.c_char_p, V],
     "ckks_plan_destroy": [V],

@@ -514,6 +514,7 @@ static int *tune_slot(ckks_context *ctx, const char *key, int &lo, int &hi) {
     if (!strcmp(key, "mac_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_mac_threads; }
     if (!strcmp(key, "inner_rescale")) { lo = 0; hi = 2; return &ctx->c.tune_inner_rescale; }
     if (!strcmp(key, "root_rescale")) { lo = 0; hi = 1; return &ctx->c.tune_root_rescale; }
+    if (!strcmp(key, "moddown")) { lo = 0; hi = 1; return &ctx->c.tune_moddown; }
     return nullptr;
 }
 

@@ -79,6 +79,13 @@ struct Acc128 {
         hi += phi + (lo < plo ? 1ull : 0ull);
         hi = hi >= q ? hi - q : hi;
     }
+    // add a 128-bit value below q * 2^64 (hi < q)
+    __device__ __forceinline__ void add(u64 vhi, u64 vlo, u64 q) {
+        lo += vlo;
+        hi += vhi + (lo < vlo ? 1ull : 0ull);
+        hi = hi >= q ? hi - q : hi;
+        hi = hi >= q ? hi - q : hi;
+    }
 };
 
 // Same accumulation without the per-term reduction: valid when the sum of

@@ -297,78 +297,98 @@ static cudaError_t relin_core(const Context &C, Ws &ws, int B, int n, int level,
         S.dst = v;
         TRY(ntt_transform(C, true, J, L, S, nullptr, st));
     }
-    // 4. key inner product
-    {
-        MacArgs M;
-        M.n_batch = B;
-        M.N = N;
-        M.level = level;
-        M.L = C.L;
-        M.K = K;
-        M.alpha = A;
-        M.n_digits = nd;
-        M.key_digits = C.dnum;
-        M.n = n;
-        M.d = D;
-        M.ext = ev;
-        M.acc = av;
-        M.keys = keys;
-        M.key_pstride = (i64)(C.L + K) * N;
-        M.mods = C.d_mods;
-        TRY(launch_mac(C, M, st));
-    }
-    // 5. ModDown, P part: z_i = [phat_i^-1 INTT(acc_i)]_{p_i}
-    {
-        LimbJobs J = jobs(B, 2, K);
-        for (int i = 0; i < K; ++i) {
-            J.slot[i] = (uint8_t)(level + i);
-            J.dslot[i] = (uint8_t)i;
-            J.prime[i] = (uint8_t)(C.L + i);
+    // 4-6. key inner product and ModDown. Combined form (Eq. 15): one MAC
+    // over every ek_t, one ModDown. Separate form (before Eq. 15, kept for
+    // measuring the saving): per ek_t its own MAC and ModDown, summed.
+    const bool separate = C.tune_moddown == 1 && n > 2;
+    const int t_lo = 2, t_hi = separate ? n : 2;
+    for (int t = t_lo; t <= t_hi; ++t) {
+        const int t_first = separate ? t : 2, t_last = separate ? t : n;
+        const bool first = t == t_lo;
+        // 4. key inner product over ek_{t_first..t_last}
+        {
+            MacArgs M;
+            M.n_batch = B;
+            M.N = N;
+            M.level = level;
+            M.L = C.L;
+            M.K = K;
+            M.alpha = A;
+            M.n_digits = nd;
+            M.key_digits = C.dnum;
+            M.n = 2 + (t_last - t_first);
+            M.d = offset(D, (i64)(t_first - 2) * D.pstride);
+            M.ext = offset(ev, (i64)(t_first - 2) * nd * ev.pstride);
+            M.ext.pstride = ev.pstride;
+            M.acc = av;
+            M.keys = keys + (size_t)(t_first - 2) * C.dnum * 2 * (C.L + K) * N;
+            M.key_pstride = (i64)(C.L + K) * N;
+            M.mods = C.d_mods;
+            TRY(launch_mac(C, M, st));
         }
-        LoadSpec L{};
-        L.mode = LD_PLAIN;
-        L.a = av;
-        StoreSpec S{};
-        S.mode = ST_SCALE;
-        S.dst = zv;
-        S.c = C.d_pscale;
-        S.c_stride = 1;
-        TRY(ntt_transform(C, false, J, L, S, nullptr, st));
-        count_op(C, OP_BCONV, 2ull * B);
-    }
-    // 6. ModDown, Q part
-    if (!ntt_moddown) {
-        // c* = INTT(D_l + P^-1 acc_l) - scBConv(z)   (Eq. 11 merged, Eq. 12)
-        LimbJobs J = jobs(B, 2, level);
-        LoadSpec L{};
-        L.mode = LD_ADD;
-        L.a = D;
-        L.b = av;
-        StoreSpec S{};
-        S.mode = ST_MODDOWN;
-        S.dst = cstar;
-        S.aux = zv;
-        S.c = C.d_ninv;
-        S.c_stride = 1;
-        S.mods = C.d_mods;
-        S.cK = C.d_cK;
-        S.K = K;
-        TRY(ntt_transform(C, false, J, L, S, nullptr, st));
-    } else {
-        // prior arrangement: C* = D_l + P^-1 acc_l - NTT(scBConv(z))
-        LimbJobs J = jobs(B, 2, level);
-        LoadSpec L{};
-        L.mode = LD_BCONVK;
-        L.b = zv;
-        L.mods = C.d_mods;
-        L.cK = C.d_cK;
-        L.K = K;
-        StoreSpec S{};
-        S.mode = ST_ADDSUB;
-        S.dst = cstar;
-        S.aux = D;
-        S.aux2 = av;
-        TRY(ntt_transform(C, true, J, L, S, nullptr, st));
+        // 5. ModDown, P part: z_i = [phat_i^-1 INTT(acc_i)]_{p_i}
+        {
+            LimbJobs J = jobs(B, 2, K);
+            for (int i = 0; i < K; ++i) {
+                J.slot[i] = (uint8_t)(level + i);
+                J.dslot[i] = (uint8_t)i;
+                J.prime[i] = (uint8_t)(C.L + i);
+            }
+            LoadSpec L{};
+            L.mode = LD_PLAIN;
+            L.a = av;
+            StoreSpec S{};
+            S.mode = ST_SCALE;
+            S.dst = zv;
+            S.c = C.d_pscale;
+            S.c_stride = 1;
+            TRY(ntt_transform(C, false, J, L, S, nullptr, st));
+            count_op(C, OP_BCONV, 2ull * B);
+        }
+        // 6. ModDown, Q part
+        if (!ntt_moddown) {
+            // c* = INTT(D_l + P^-1 acc_l) - scBConv(z)   (Eq. 11 merged, Eq. 12);
+            // later keys of the separate form: INTT(P^-1 acc_l) - scBConv(z)
+            // into the free y buffer, then added to c*
+            LimbView tmp = view(y, yv.bstride, (i64)level * N);
+            LimbJobs J = jobs(B, 2, level);
+            LoadSpec L{};
+            L.mode = first ? LD_ADD : LD_PLAIN;
+            L.a = first ? D : av;
+            L.b = av;
+            StoreSpec S{};
+            S.mode = ST_MODDOWN;
+            S.dst = first ? cstar : tmp;
+            S.aux = zv;
+            S.c = C.d_ninv;
+            S.c_stride = 1;
+            S.mods = C.d_mods;
+            S.cK = C.d_cK;
+            S.K = K;
+            TRY(ntt_transform(C, false, J, L, S, nullptr, st));
+            if (!first) TRY(launch_add_limbs(C, cstar, tmp, B, 2, level, st));
+        } else {
+            // prior arrangement: C* = D_l + P^-1 acc_l - NTT(scBConv(z)); later
+            // keys of the separate form add to C* in place
+            LimbJobs J = jobs(B, 2, level);
+            LoadSpec L{};
+            L.mode = LD_BCONVK;
+            L.b = zv;
+            L.mods = C.d_mods;
+            L.cK = C.d_cK;
+            L.K = K;
+            StoreSpec S{};
+            S.mode = ST_ADDSUB;
+            S.dst = cstar;
+            S.aux = first ? D : cstar;
+            S.aux2 = av;
+            // the first phase's intermediate must not overwrite C* while C*
+            // is also the addend: stage it in the free y buffer
+            StoreSpec mid{};
+            mid.mode = ST_LAZY;
+            mid.dst = view(y, yv.bstride, (i64)level * N);
+            TRY(ntt_transform(C, true, J, L, S, first ? nullptr : &mid, st));
+        }
     }
     return cudaSuccess;
 }

@@ -125,6 +125,9 @@ struct Context {
     // reformulations): see multi_rs and run_mul_k in engine.cu
     int tune_inner_rescale = 0;
     int tune_root_rescale = 0;
+    // key switching: 0 = one ModDown over the summed keys (Eq. 15), 1 = one
+    // ModDown per key, summed afterwards (the form before Eq. 15)
+    int tune_moddown = 0;
 };
 
 // Records CUDA events around one launch on its stream when the hook is on;

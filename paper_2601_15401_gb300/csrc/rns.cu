@@ -48,15 +48,46 @@ __global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
 #pragma unroll
         for (int a = 0; a < MAXT; ++a) y[a] = a < ny ? src[(i64)a * A.child[c].pstride] : 0ull;
         u64 nxt[MAXT];
+        if (ny == 2) {
+            // times a ciphertext (y0 + y1 s): Karatsuba on pairs of the running
+            // tuple (Fig. 2(b)): for (c_a, c_{a+1}) the cross term
+            // c_a y1 + c_{a+1} y0 = (c_a + c_{a+1})(y0 + y1) - c_a y0 - c_{a+1} y1,
+            // an exact non-negative integer, so it stays in the 128-bit sums.
+            Acc128 acc[MAXT];
 #pragma unroll
-        for (int t = 0; t < MAXT; ++t) {
-            Acc128 acc;
-            acc.zero();
+            for (int t = 0; t < MAXT; ++t) acc[t].zero();
+            const u64 ys = y[0] + y[1];  // < 2q, not reduced
 #pragma unroll
-            for (int a = 0; a <= t; ++a) {
-                if (a < ncur && t - a < ny) acc.mac(cur[a], y[t - a], q);
+            for (int a = 0; a < MAXT; a += 2) {
+                if (a + 1 < ncur && a + 2 < MAXT) {
+                    const u64 p1h = mulhi64(cur[a], y[0]), p1l = cur[a] * y[0];
+                    const u64 p2h = mulhi64(cur[a + 1], y[1]), p2l = cur[a + 1] * y[1];
+                    const u64 s = cur[a] + cur[a + 1];
+                    u64 p3l = s * ys, p3h = mulhi64(s, ys);
+                    // p3 -= p1 + p2 (128-bit; the result is c_a y1 + c_{a+1} y0 >= 0)
+                    u64 bl = p1l + p2l, bh = p1h + p2h + (bl < p1l ? 1ull : 0ull);
+                    u64 rl = p3l - bl, rh = p3h - bh - (p3l < bl ? 1ull : 0ull);
+                    acc[a].add(p1h, p1l, q);
+                    acc[a + 1].add(rh, rl, q);
+                    acc[a + 2].add(p2h, p2l, q);
+                } else if (a < ncur && a + 1 >= ncur) {
+                    acc[a].mac(cur[a], y[0], q);
+                    if (a + 1 < MAXT) acc[a + 1].mac(cur[a], y[1], q);
+                }
             }
-            nxt[t] = t < ncur + ny - 1 ? redc(acc.hi, acc.lo, m) : 0ull;
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) nxt[t] = t < ncur + 1 ? redc(acc[t].hi, acc[t].lo, m) : 0ull;
+        } else {
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) {
+                Acc128 acc;
+                acc.zero();
+#pragma unroll
+                for (int a = 0; a <= t; ++a) {
+                    if (a < ncur && t - a < ny) acc.mac(cur[a], y[t - a], q);
+                }
+                nxt[t] = t < ncur + ny - 1 ? redc(acc.hi, acc.lo, m) : 0ull;
+            }
         }
         ncur = ncur + ny - 1;
 #pragma unroll
@@ -288,7 +319,8 @@ __global__ void __launch_bounds__(kThreads) signed_to_res_kernel(const i64 *v, u
     const int i = (int)(gid % N);
     const i64 s = v[i];
     const u64 q = mods[x].q;
-    out[gid] = s >= 0 ? ((u64)s) % q : q - (((u64)(-s)) % q);
+    const u64 r = s >= 0 ? ((u64)s) % q : ((u64)(-s)) % q;
+    out[gid] = (s >= 0 || r == 0) ? r : q - r;
 }
 
 cudaError_t launch_signed_to_res(const Context &C, const long long *v, u64 *out, cudaStream_t st) {
@@ -317,6 +349,31 @@ cudaError_t launch_pointwise_mul(const Context &C, u64 *St, const u64 *S, cudaSt
     count_kernel(C);
     pointwise_mul_kernel<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(
         St, S, C.L + C.K, C.N, C.d_mods, C.d_r2);
+    return cudaGetLastError();
+}
+
+// dst <- dst + src over [batch][polys][level][N] limb views (limb x mod q_x)
+__global__ void __launch_bounds__(kThreads) add_limbs_kernel(LimbView dst, LimbView src, int polys, int level, int N,
+                                                             const ModQ *mods) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 per_poly = (i64)level * N;
+    if (gid >= per_poly * polys) return;
+    const int b = blockIdx.y;
+    const int p = (int)(gid / per_poly);
+    const i64 r = gid % per_poly;
+    const int x = (int)(r / N);
+    u64 *d = dst.ptr + (i64)b * dst.bstride + (i64)p * dst.pstride + r;
+    const u64 v = src.ptr[(i64)b * src.bstride + (i64)p * src.pstride + r];
+    *d = add_mod(*d, v, mods[x].q);
+}
+
+cudaError_t launch_add_limbs(const Context &C, LimbView dst, LimbView src, int batch, int polys, int level,
+                             cudaStream_t st) {
+    const i64 total = (i64)polys * level * C.N;
+    if (total == 0 || batch == 0) return cudaSuccess;
+    count_kernel(C);
+    dim3 grid((unsigned)((total + kThreads - 1) / kThreads), (unsigned)batch);
+    add_limbs_kernel<<<grid, kThreads, 0, st>>>(dst, src, polys, level, C.N, C.d_mods);
     return cudaGetLastError();
 }
 

@@ -50,6 +50,8 @@ cudaError_t launch_rschain(const Context &C, const RsChainArgs &A, cudaStream_t 
 cudaError_t launch_keyprep(const Context &C, u64 *keys, long long n_rows, cudaStream_t st);
 cudaError_t launch_signed_to_res(const Context &C, const long long *v, u64 *out, cudaStream_t st);
 cudaError_t launch_pointwise_mul(const Context &C, u64 *St, const u64 *S, cudaStream_t st);
+cudaError_t launch_add_limbs(const Context &C, LimbView dst, LimbView src, int batch, int polys, int level,
+                             cudaStream_t st);
 cudaError_t launch_keygen(const Context &C, const u64 *S, const u64 *St, const u64 *E, const u64 *a, u64 *ek,
                           int beta, cudaStream_t st);
 

@@ -40,6 +40,7 @@ class Request:
     partition: str | None = None
     admitted: float = -1.0
     done: float = -1.0
+    error: str | None = None
 
     @property
     def shape(self):
@@ -63,8 +64,11 @@ class Scheduler:
     backend must provide: n_streams, footprint(shape, batch) -> bytes,
     launch(batch) -> handle, poll(handle) -> bool, and optional finish(batch)."""
 
-    def __init__(self, backend, cap_bytes: int, max_batch: int = 8, max_queue: int = 100000):
+    def __init__(self, backend, cap_bytes: int, max_batch: int = 8, max_queue: int = 100000,
+                 timeout_s: float | None = None):
         self.be = backend
+        self.timeout_s = timeout_s      # watchdog: a batch running longer is failed
+        self.failed: list[Request] = []
         self.cap = cap_bytes
         self.max_batch = max_batch
         self.max_queue = max_queue
@@ -100,6 +104,18 @@ class Scheduler:
         memory allow. Returns the number of batches launched."""
         still = []
         for b in self.running:
+            if self.timeout_s is not None and now is not None and now - b.launched > self.timeout_s \
+                    and not self.be.poll(b.handle):
+                # the batch missed its deadline: fail its requests and keep its
+                # stream and memory out of use (the work may still be running)
+                for r in b.reqs:
+                    r.done = now
+                    r.error = "timeout"
+                self.failed.extend(b.reqs)
+                abandon = getattr(self.be, "abandon", None)
+                if abandon:
+                    abandon(b)
+                continue
             if self.be.poll(b.handle):
                 t = time.perf_counter() if now is None else now
                 for r in b.reqs:
@@ -143,6 +159,10 @@ class Scheduler:
 
     def idle(self) -> bool:
         return not self.running and self.pending() == 0
+
+    def healthy_streams(self) -> int:
+        """Streams not lost to timed-out batches."""
+        return len(self.free_streams) + len(self.running)
 
 
 # ---------------------------------------------------------------------------
@@ -218,6 +238,12 @@ class GpuBackend:
 
     def poll(self, handle) -> bool:
         return handle[0].query()
+
+    def abandon(self, b: Batch):
+        """A timed-out batch: keep its buffers alive (the device may still be
+        using them) and never reuse its stream."""
+        self._abandoned = getattr(self, "_abandoned", [])
+        self._abandoned.append(b.handle)
 
     def finish(self, b: Batch):
         """Completed batch: hand results over (kept only when asked; a

@@ -271,6 +271,49 @@ def test_rescale_forms_give_identical_products(S12, key, value, k):
     assert np.array_equal(other, base)
 
 
+@pytest.mark.parametrize("root_rescale", [0, 1])
+@pytest.mark.parametrize("k", [3, 5, 9])
+def test_separate_moddowns_match_oracle(S12, k, root_rescale):
+    """One ModDown per ek_t (the form Eq. 15 replaces), in both root
+    arrangements, against the oracle's separate form."""
+    level = 7 if k > 8 else 6
+    cts = _inputs(S12, k, level, 216, 10 * k)
+    S12.ctx.tune_set("moddown", 1)
+    S12.ctx.tune_set("root_rescale", root_rescale)
+    try:
+        out = _run_mul_k(S12, cts, level)
+    finally:
+        S12.ctx.tune_set("moddown", 0)
+        S12.ctx.tune_set("root_rescale", 0)
+    want = O.mul_k(S12.octx, [oracle_tuple(c) for c in cts], S12.okeys, separate_moddown=True)
+    assert np.array_equal(host(out.data)[:, :out.level], want.data)
+
+
+def test_separate_moddowns_relin_parity_and_counts(S12):
+    """ckks_relin in the separate form: residues and the (n - 2) extra
+    ModDowns (K + level limb INTTs per polynomial each)."""
+    import paper_2601_15401_gb300 as G
+    n, level = 5, 6
+    g = synth.rng(217)
+    d = np.stack([synth.uniform_residues(g, S12.params.q[:level], S12.params.N) for _ in range(n + 1)])
+    ws = S12.ws(S12.ctx.relin_workspace_size(n, level))
+    counts = {}
+    for mode in (0, 1):
+        S12.ctx.tune_set("moddown", mode)
+        try:
+            out = G.Tuple.wrap(dev(np.zeros((2, level, S12.params.N), dtype=np.uint64)))
+            S12.ctx.counters(reset=True)
+            S12.ctx.relin(G.Tuple.wrap(dev(d)), S12.evk, out, ws, out_ntt=False)
+            counts[mode] = S12.ctx.counters(reset=True)
+        finally:
+            S12.ctx.tune_set("moddown", 0)
+        want = O.relin_coef(S12.octx, d, S12.okeys, level, separate=bool(mode))
+        assert np.array_equal(host(out.data), want), mode
+    extra = counts[1]["limb_intt"] - counts[0]["limb_intt"]
+    assert extra == (n - 2) * 2 * (S12.params.K + level)
+    assert counts[1]["limb_ntt"] == counts[0]["limb_ntt"]
+
+
 def test_table_iv_counts_for_each_rescale_form():
     """Table IV: mu combined rescales cost mu INTT + (L - mu) NTT per
     polynomial (Algorithm 1); the baseline costs L INTT + (L - mu) NTT."""

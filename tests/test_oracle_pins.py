@@ -333,6 +333,35 @@ def test_relocated_3input_equals_prior_arrangement():
     assert np.array_equal(x.data, prior)
 
 
+def test_separate_moddowns_differ_by_wrap_count():
+    """One ModDown per ek_t (the form before Eq. 15) against one ModDown of
+    the sum: ModDown is linear except that each [.]_{p_i} of Eq. 5 wraps
+    once per extra addend at most, and every wrap adds p_i (P / p_i) = P
+    before the division by P. So separate - combined = -W in every limb,
+    the same integer W in [0, K (n - 2)] for each coefficient."""
+    params = synth.make_params(5, [50] * 5, 3, 2)  # K = 3
+    ctx = ckks.Ctx(params)
+    n = 5
+    km = synth.key_material(params, n, 17)
+    keys = ckks.keygen_all(ctx, km, n)
+    g = synth.rng(97)
+    level = 5
+    d = np.stack([synth.uniform_residues(g, ctx.q[:level], ctx.N) for _ in range(n + 1)])
+    comb = ckks.relin_coef(ctx, d, keys, level)
+    sep = ckks.relin_coef(ctx, d, keys, level, separate=True)
+    assert not np.array_equal(comb, sep)  # wraps do happen at these sizes
+    for l in range(2):
+        W = None
+        for j, qj in enumerate(ctx.q[:level]):
+            w = (comb[l][j].astype(object) - sep[l][j].astype(object)) % qj
+            W = w if W is None else W
+            assert np.array_equal(w, W)
+        assert max(W) <= ctx.K * (n - 2)
+    # and the NTT-domain arrangement is the same function
+    sep_ntt = ckks.relin_ntt(ctx, d, keys, level, separate=True)
+    assert np.array_equal(sep_ntt, np.stack([ckks.ntt_poly(sep[l], ctx.q[:level]) for l in range(2)]))
+
+
 def test_inner_node_rescale_forms_agree():
     params = synth.make_params(4, [50] * 6, 2, 3)
     ctx = ckks.Ctx(params)

@@ -97,3 +97,29 @@ def test_latency_stats():
         r.done = (i + 1) / 1000.0
     st = latency_stats(rs)
     assert st["p50_ms"] == pytest.approx(50.0) and st["p99_ms"] == pytest.approx(99.0)
+
+
+class StuckBackend(FakeBackend):
+    """Injects a fault on the host: every batch of shape k = 7 never completes."""
+
+    def launch(self, b):
+        self.launched.append(b)
+        return [10 ** 9 if b.shape[1] == 7 else self.polls]
+
+    def abandon(self, b):
+        self.abandoned = getattr(self, "abandoned", 0) + 1
+
+
+def test_watchdog_fails_a_stuck_batch_and_the_rest_completes():
+    be = StuckBackend(n_streams=2, polls=1)
+    s = Scheduler(be, cap_bytes=10 ** 9, max_batch=4, timeout_s=1.0)
+    s.submit(req(0, k=7))
+    for i in range(1, 6):
+        s.submit(req(i, k=3, t=0.1))
+    now = 0.0
+    while not s.idle() and now < 10:
+        s.step(now)
+        now += 0.5
+    assert [r.rid for r in s.failed] == [0] and s.failed[0].error == "timeout"
+    assert sorted(r.rid for r in s.completed) == [1, 2, 3, 4, 5]
+    assert be.abandoned == 1 and s.healthy_streams() == 1
