@@ -128,6 +128,22 @@ void ckks_evk_set_destroy(ckks_evk_set *set);
  * [N] (device); exact while |message| < q_0 q_1 / 2. Workspace for all
  * three: ckks_encrypt_workspace_size. */
 int ckks_encrypt_workspace_size(const ckks_context *ctx, size_t *bytes);
+/* Canonical-embedding encoding and decoding (Section II), N/2 complex slots
+ * per message, slot j at zeta_j = exp(i pi 5^j / N). ckks_encode: z device
+ * double [batch][N/2][2] (re, im) -> m device int64 [batch][N], m_i =
+ * round((2/N) Re sum_j scale z_j zeta_j^-i) (round half to even), computed
+ * in double precision by a four-step FFT, so m carries the FFT's rounding
+ * (about log2(N) ulps of scale |z|); |scale z| must stay below 2^62.
+ * ckks_decode: m device double [batch][N] (e.g. ckks_decrypt's output)
+ * -> z device double [batch][N/2][2], z_j = sum_i m_i zeta_j^i / scale.
+ * Workspace (16-byte aligned): ckks_embed_workspace_size(batch) bytes.
+ * CKKS_EINVAL for batch 0 or above 65535, scale <= 0, N < 4. Both are
+ * asynchronous on `stream`. */
+int ckks_embed_workspace_size(const ckks_context *ctx, uint32_t batch, size_t *bytes);
+int ckks_encode(ckks_context *ctx, const double *z, uint32_t batch, double scale, int64_t *m, void *workspace,
+                size_t ws_bytes, void *stream);
+int ckks_decode(ckks_context *ctx, const double *m, uint32_t batch, double scale, double *z, void *workspace,
+                size_t ws_bytes, void *stream);
 int ckks_public_key(ckks_context *ctx, const int64_t *s, const uint64_t *a, const int64_t *e, uint64_t *pk,
                     void *workspace, size_t ws_bytes, void *stream);
 int ckks_encrypt(ckks_context *ctx, const int64_t *m, const int64_t *v, const int64_t *e0, const int64_t *e1,
@@ -135,6 +151,39 @@ int ckks_encrypt(ckks_context *ctx, const int64_t *m, const int64_t *v, const in
                  void *stream);
 int ckks_decrypt(ckks_context *ctx, const ckks_tuple *ct, const int64_t *s, double *out, void *workspace,
                  size_t ws_bytes, void *stream);
+
+/* -------------------------------------------------------------- rotation
+ * Slot rotation by a Galois automorphism sigma_g: a(X) -> a(X^g), g odd,
+ * 1 <= g < 2N (Section II's canonical embedding: g = 5^r mod 2N moves slot
+ * j + r to slot j, g = 2N - 1 conjugates every slot). Key switching back to
+ * s reuses the relinearisation steps (ModUp, key MAC, ModDown) with one key.
+ * ckks_galois_element: g = 5^r mod 2N for any integer r (r < 0 rotates
+ * the other way). CKKS_EINVAL for N < 4.
+ * ckks_automorphism: out = sigma_g(in) for every polynomial of an NTT-domain
+ * tuple (a permutation of each limb: out[i] = in[brv((g (2 brv(i) + 1) mod
+ * 2N - 1) / 2)]); same level and scale; out must not overlap in
+ * (CKKS_EINVAL if out->data == in->data; partial overlap is undefined).
+ * ckks_keygen_galois: the Galois key of g from s, a, e (layouts as in
+ * ckks_keygen_evk with t_max = 2: a device [dnum][L+K][N], e device int64
+ * [dnum][N], keys [dnum][2][L+K][N]): gk_beta = (-a_beta s + e_beta +
+ * [Q limb] P G_beta sigma_g(s), a_beta). Workspace:
+ * ckks_keygen_workspace_size. Adopt it with ckks_evk_set_create(ctx, 2,
+ * keys, ...): a Galois key is a one-key set whose key sits where ek_2 would.
+ * ckks_rotate / ckks_rotate_batch: out = (sigma c_0 + [P^-1 sigma(c_1)
+ * gk_0], [P^-1 sigma(c_1) gk_1]) with ModDown finished in the NTT domain;
+ * same level and scale as the input; decrypts under s to sigma_g of the
+ * message. Batch tuples evenly spaced as in ckks_mul2_batch; out may be
+ * the input. Workspace: ckks_rotate_workspace_size. Errors: CKKS_EINVAL
+ * (g even or >= 2N, shapes), CKKS_ELEVEL, CKKS_ENOMEM. */
+int ckks_galois_element(const ckks_context *ctx, int32_t r, uint32_t *g);
+int ckks_automorphism(ckks_context *ctx, const ckks_tuple *in, uint32_t g, ckks_tuple *out, void *stream);
+int ckks_keygen_galois(ckks_context *ctx, uint32_t g, const int64_t *s, const uint64_t *a, const int64_t *e,
+                       uint64_t *keys, void *workspace, size_t ws_bytes, void *stream);
+int ckks_rotate_workspace_size(const ckks_context *ctx, uint32_t level, uint32_t batch, size_t *bytes);
+int ckks_rotate(ckks_context *ctx, const ckks_tuple *in, uint32_t g, const ckks_evk_set *gk, ckks_tuple *out,
+                void *workspace, size_t ws_bytes, void *stream);
+int ckks_rotate_batch(ckks_context *ctx, const ckks_tuple *in, uint32_t batch, uint32_t g, const ckks_evk_set *gk,
+                      ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------- plans
  * ckks_plan_create: the partition tree of a k-input multiply (2 <= k <= 12)

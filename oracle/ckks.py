@@ -448,6 +448,24 @@ def decode(N: int, m: list[int], scale: float) -> np.ndarray:
     return (zeta[:, None] ** i[None, :] * mf[None, :]).sum(axis=1)
 
 
+def decode_slot(N: int, m, scale: float, j: int) -> complex:
+    """One slot, z_j = sum_i m_i zeta_j^i / scale, with the exponent of
+    zeta_j^i = omega^(5^j i) reduced mod 2N in integers (no power error)."""
+    e = pow(5, j, 2 * N)
+    i = np.arange(N, dtype=np.int64)
+    ang = np.pi * ((e * i) % (2 * N)).astype(np.float64) / N
+    mf = np.array([float(x) for x in m], dtype=np.float64) / scale
+    return complex(np.sum(mf * np.cos(ang)), np.sum(mf * np.sin(ang)))
+
+
+def encode_coef(N: int, z: np.ndarray, scale: float, i: int) -> float:
+    """One coefficient before rounding: (2/N) Re sum_j scale z_j zeta_j^-i,
+    exponents reduced mod 2N in integers."""
+    e = np.array([pow(5, j, 2 * N) for j in range(N // 2)], dtype=np.int64)
+    ang = -np.pi * ((e * i) % (2 * N)).astype(np.float64) / N
+    return float((2.0 / N) * np.sum(scale * (z.real * np.cos(ang) - z.imag * np.sin(ang))))
+
+
 def public_key(ctx: Ctx, s, a, e):
     """pk = (-a s + e, a) on the Q limbs, NTT domain (a given NTT domain)."""
     S = ntt_poly(np.stack([ring.from_signed(s, x) for x in ctx.q]), ctx.q)
@@ -496,3 +514,68 @@ def decrypt(ctx: Ctx, ct: np.ndarray, s) -> list[int]:
         sj = ring.from_signed(s, qj)
         rows.append(ring.addmod(c[0][j], ring.negacyclic_mul(c[1][j], sj, qj), qj))
     return crt_centered(np.stack(rows), primes)
+
+
+# ---------------------------------------------------------------------------
+# Galois automorphisms and slot rotation (Section II's encoding; key switch
+# as in Eq. 3-5 with the key of sigma_g(s))
+# ---------------------------------------------------------------------------
+def galois_element(r: int, N: int) -> int:
+    """g = 5^r mod 2N: sigma_g moves slot j + r of the encoding to slot j."""
+    return pow(5, r % (N // 2), 2 * N)
+
+
+def automorphism_coef(a, g: int, q: int) -> np.ndarray:
+    """a(X^g) mod (X^N + 1, q) from its definition: X^i -> X^(g i), and
+    X^(N + j) = -X^j. `a` holds residues mod q."""
+    N = len(a)
+    out = np.zeros(N, dtype=np.uint64)
+    for i in range(N):
+        j = (g * i) % (2 * N)
+        v = int(a[i]) % q
+        if j < N:
+            out[j] = (int(out[j]) + v) % q
+        else:
+            out[j - N] = (int(out[j - N]) - v) % q
+    return out
+
+
+def automorphism_signed(s, g: int) -> np.ndarray:
+    """The same map on a signed integer polynomial (the secret)."""
+    N = len(s)
+    out = np.zeros(N, dtype=np.int64)
+    for i in range(N):
+        j = (g * i) % (2 * N)
+        if j < N:
+            out[j] += int(s[i])
+        else:
+            out[j - N] -= int(s[i])
+    return out
+
+
+def automorphism_ntt(A: np.ndarray, g: int, primes) -> np.ndarray:
+    """sigma_g of an NTT-domain [limbs][N] array: back to coefficients,
+    the definition, forward again."""
+    a = intt_poly(A, primes)
+    return ntt_poly(np.stack([automorphism_coef(a[j], g, qj) for j, qj in enumerate(primes)]), primes)
+
+
+def galois_keygen(ctx: Ctx, km_s, a, e, g: int):
+    """gk[beta] = (-a s + e + [Q limb] P G_beta sigma_g(s), a): the
+    evaluation-key construction with sigma_g(s) in place of s^t. a: [dnum]
+    NTT-domain [L + K][N]; e: [dnum] signed [N]."""
+    S = secret_ntt(ctx, km_s)
+    Sg = secret_ntt(ctx, automorphism_signed(km_s, g))
+    return [keygen(ctx, km_s, a[b], e[b], 2, b, S, Sg) for b in range(ctx.dnum)]
+
+
+def rotate(ctx: Ctx, ct: Tup, g: int, gkey) -> Tup:
+    """(sigma c_0, sigma c_1) switched back to s: the relinearisation of
+    (sigma c_0, 0, sigma c_1) with the Galois key in the place of ek_2,
+    ModDown finished in the NTT domain."""
+    level = ct.level
+    primes = ctx.q[:level]
+    c0 = automorphism_ntt(ct.data[0], g, primes)
+    c1 = automorphism_ntt(ct.data[1], g, primes)
+    d = np.stack([c0, np.zeros_like(c0), c1])
+    return Tup(relin_ntt(ctx, d, [gkey], level), ct.scale)

@@ -23,6 +23,16 @@ TABLE_II = {
 }
 
 
+def _as_real_pairs(z):
+    """A contiguous complex128 or float64 [..., 2] tensor as float64 pairs."""
+    import torch
+    if z.dtype == torch.complex128:
+        z = torch.view_as_real(z)
+    if z.dtype != torch.float64 or not z.is_contiguous():
+        raise ValueError("slots must be a contiguous complex128 (or float64 [..., 2]) tensor")
+    return z
+
+
 class _Params(ctypes.Structure):
     _fields_ = [("log_n", ctypes.c_uint32), ("L", ctypes.c_uint32), ("K", ctypes.c_uint32),
                 ("dnum", ctypes.c_uint32), ("q", ctypes.POINTER(ctypes.c_uint64)),
@@ -135,6 +145,28 @@ class Context:
         _check(lib().ckks_encrypt_workspace_size(self._h, ctypes.byref(n)), "ckks_encrypt_workspace_size")
         return n.value
 
+    def embed_workspace_size(self, batch: int = 1) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ckks_embed_workspace_size(self._h, batch, ctypes.byref(n)), "ckks_embed_workspace_size")
+        return n.value
+
+    def encode(self, z, scale: float, m, workspace, stream=None):
+        """z: complex128 (or float64 [..., 2]) CUDA tensor [batch][N/2];
+        m: int64 CUDA tensor [batch][N] <- rounded canonical-embedding coefficients."""
+        zr = _as_real_pairs(z)
+        batch = zr.numel() // self.N
+        _check(lib().ckks_encode(self._h, zr.data_ptr(), batch, float(scale), m.data_ptr(), workspace.data_ptr(),
+                                 workspace.numel() * workspace.element_size(), _stream(stream)), "ckks_encode")
+        return m
+
+    def decode(self, m, scale: float, z, workspace, stream=None):
+        """m: float64 CUDA tensor [batch][N]; z: complex128 CUDA tensor [batch][N/2]."""
+        zr = _as_real_pairs(z)
+        batch = m.numel() // self.N
+        _check(lib().ckks_decode(self._h, m.data_ptr(), batch, float(scale), zr.data_ptr(), workspace.data_ptr(),
+                                 workspace.numel() * workspace.element_size(), _stream(stream)), "ckks_decode")
+        return z
+
     def public_key(self, s, a, e, pk, workspace, stream=None):
         _check(lib().ckks_public_key(self._h, s.data_ptr(), a.data_ptr(), e.data_ptr(), pk.data_ptr(),
                                      workspace.data_ptr(), workspace.numel() * workspace.element_size(),
@@ -154,6 +186,46 @@ class Context:
         _check(lib().ckks_decrypt(self._h, ctypes.byref(c), s.data_ptr(), out.data_ptr(), workspace.data_ptr(),
                                   workspace.numel() * workspace.element_size(), _stream(stream)), "ckks_decrypt")
         return out
+
+    # -------------------------------------------------------------- rotation
+    def galois_element(self, r: int) -> int:
+        """g = 5^r mod 2N (the automorphism that rotates the slots by r)."""
+        g = ctypes.c_uint32()
+        _check(lib().ckks_galois_element(self._h, int(r), ctypes.byref(g)), "ckks_galois_element")
+        return g.value
+
+    def automorphism(self, t: Tuple, g: int, out: Tuple, stream=None) -> Tuple:
+        c, o = t.c(), out.c()
+        _check(lib().ckks_automorphism(self._h, ctypes.byref(c), g, ctypes.byref(o), _stream(stream)),
+               "ckks_automorphism")
+        out.level, out.n_polys, out.ntt_form, out.scale, out.poly_stride = o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride
+        return out
+
+    def keygen_galois(self, g: int, s, a, e, keys, workspace, stream=None):
+        """keys [dnum][2][L+K][N] <- the Galois key of g; adopt with evk_set(2, keys)."""
+        _check(lib().ckks_keygen_galois(self._h, g, s.data_ptr(), a.data_ptr(), e.data_ptr(), keys.data_ptr(),
+                                        workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                        _stream(stream)), "ckks_keygen_galois")
+
+    def rotate_workspace_size(self, level: int, batch: int = 1) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ckks_rotate_workspace_size(self._h, level, batch, ctypes.byref(n)), "ckks_rotate_workspace_size")
+        return n.value
+
+    def rotate_batch(self, cts, g: int, gk, outs, workspace, stream=None):
+        """cts, outs: lists over the batch of Tuples (evenly strided)."""
+        B = len(cts)
+        ii = (_Tuple * B)(*[t.c() for t in cts])
+        oo = (_Tuple * B)(*[t.c() for t in outs])
+        _check(lib().ckks_rotate_batch(self._h, ii, B, g, gk._h, oo, workspace.data_ptr(),
+                                       workspace.numel() * workspace.element_size(), _stream(stream)),
+               "ckks_rotate_batch")
+        for o, r in zip(outs, oo):
+            o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride = r.level, r.n_polys, r.ntt_form, r.scale, r.poly_stride
+        return outs
+
+    def rotate(self, ct: Tuple, g: int, gk, out: Tuple, workspace, stream=None) -> Tuple:
+        return self.rotate_batch([ct], g, gk, [out], workspace, stream)[0]
 
     def evk_set(self, t_max: int, keys, stream=None) -> "EvkSet":
         h = ctypes.c_void_p()

@@ -31,7 +31,16 @@ SIGNATURES = {
     "ckks_keygen_workspace_size": [V, V],
     "ckks_keygen_evk": [V, U32, V, V, V, V, V, SZ, V],
     "ckks_evk_set_create": [V, U32, V, V, V],
+    "ckks_galois_element": [V, I, V],
+    "ckks_automorphism": [V, V, U32, V, V],
+    "ckks_keygen_galois": [V, U32, V, V, V, V, V, SZ, V],
+    "ckks_rotate_workspace_size": [V, U32, U32, V],
+    "ckks_rotate": [V, V, U32, V, V, V, SZ, V],
+    "ckks_rotate_batch": [V, V, U32, U32, V, V, V, SZ, V],
     "ckks_encrypt_workspace_size": [V, V],
+    "ckks_embed_workspace_size": [V, U32, V],
+    "ckks_encode": [V, V, U32, D, V, V, SZ, V],
+    "ckks_decode": [V, V, U32, D, V, V, SZ, V],
     "ckks_public_key": [V, V, V, V, V, V, SZ, V],
     "ckks_encrypt": [V, V, V, V, V, V, U32, V, V, SZ, V],
     "ckks_decrypt": [V, V, V, V, V, SZ, V],

@@ -389,6 +389,135 @@ int ckks_relin(ckks_context *ctx, const ckks_tuple *d, const ckks_evk_set *evk, 
     return CKKS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Galois automorphisms and rotation
+// ---------------------------------------------------------------------------
+static bool galois_ok(const Context &C, uint32_t g) { return (g & 1u) && g < (uint32_t)(2 * C.N); }
+
+int ckks_galois_element(const ckks_context *ctx, int32_t r, uint32_t *g) {
+    if (!ctx || !g) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    if (C.N < 4) return CKKS_EINVAL;
+    const uint64_t M = 2ull * (uint64_t)C.N, half = (uint64_t)C.N / 2;  // 5 has order N/2 mod 2N
+    uint64_t e = (uint64_t)(((int64_t)r % (int64_t)half + (int64_t)half) % (int64_t)half);
+    uint64_t x = 1, b = 5 % M;
+    for (; e; e >>= 1, b = b * b % M)
+        if (e & 1) x = x * b % M;
+    *g = (uint32_t)x;
+    return CKKS_OK;
+}
+
+int ckks_automorphism(ckks_context *ctx, const ckks_tuple *in, uint32_t g, ckks_tuple *out, void *stream) {
+    if (!ctx || !in || !out || !out->data) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    if (!tuple_ok(in, C.L) || !in->ntt_form || !galois_ok(C, g) || out->data == in->data) return CKKS_EINVAL;
+    if (out->poly_stride == 0) out->poly_stride = in->level;
+    if (out->poly_stride < in->level) return CKKS_EINVAL;
+    AutoMap map{};
+    map.n_out = (int)in->n_polys;
+    for (int p = 0; p < map.n_out; ++p) map.src[p] = p;
+    cudaSetDevice(C.device);
+    cudaError_t err = launch_automorphism(C, tview(*in, C.N), tview(*out, C.N), map, 1, (int)in->level, g, S(stream));
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    out->n_polys = in->n_polys;
+    out->level = in->level;
+    out->ntt_form = 1;
+    out->scale = in->scale;
+    return CKKS_OK;
+}
+
+int ckks_keygen_galois(ckks_context *ctx, uint32_t g, const int64_t *s, const uint64_t *a, const int64_t *e,
+                       uint64_t *keys, void *workspace, size_t ws_bytes, void *stream) {
+    if (!ctx || !s || !a || !e || !keys || !workspace) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    if (!galois_ok(C, g)) return CKKS_EINVAL;
+    size_t need;
+    ckks_keygen_workspace_size(ctx, &need);
+    if (ws_bytes < need) return CKKS_ENOMEM;
+    cudaSetDevice(C.device);
+    const int NP = C.L + C.K;
+    const size_t plane = (size_t)NP * C.N;
+    u64 *Sb = (u64 *)workspace, *Sg = Sb + plane, *E = Sg + plane;
+    cudaStream_t st = S(stream);
+    LimbJobs J;
+    memset(&J, 0, sizeof(J));
+    J.n_batch = 1;
+    J.n_polys = 1;
+    J.n_limbs = NP;
+    for (int i = 0; i < NP; ++i) J.slot[i] = J.dslot[i] = J.prime[i] = (uint8_t)i;
+    auto ntt_plane = [&](u64 *buf) {
+        LoadSpec L{};
+        L.mode = LD_PLAIN;
+        L.a = LimbView{buf, 0, (i64)plane};
+        StoreSpec Sp{};
+        Sp.mode = ST_REDUCE;
+        Sp.dst = L.a;
+        return ntt_transform(C, true, J, L, Sp, nullptr, st);
+    };
+    // S = NTT(s), S_g = sigma_g(S) (a permutation in the NTT domain)
+    cudaError_t err = launch_signed_to_res(C, (const long long *)s, Sb, st);
+    if (err == cudaSuccess) err = ntt_plane(Sb);
+    if (err == cudaSuccess) {
+        AutoMap map{};
+        map.n_out = 1;
+        map.src[0] = 0;
+        err = launch_automorphism(C, LimbView{Sb, 0, (i64)plane}, LimbView{Sg, 0, (i64)plane}, map, 1, NP, g, st);
+    }
+    for (int b = 0; b < C.dnum && err == cudaSuccess; ++b) {
+        err = launch_signed_to_res(C, (const long long *)(e + (size_t)b * C.N), E, st);
+        if (err == cudaSuccess) err = ntt_plane(E);
+        if (err == cudaSuccess)
+            err = launch_keygen(C, Sb, Sg, E, (const u64 *)a + b * plane, (u64 *)keys + (size_t)b * 2 * plane, b, st);
+    }
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    return CKKS_OK;
+}
+
+int ckks_rotate_workspace_size(const ckks_context *ctx, uint32_t level, uint32_t batch, size_t *bytes) {
+    if (!ctx || !bytes || batch < 1) return CKKS_EINVAL;
+    if (level < 1 || level > (uint32_t)ctx->c.L) return CKKS_ELEVEL;
+    *bytes = rotate_ws_bytes(ctx->c, (int)level, (int)batch);
+    return CKKS_OK;
+}
+
+int ckks_rotate_batch(ckks_context *ctx, const ckks_tuple *in, uint32_t batch, uint32_t g, const ckks_evk_set *gk,
+                      ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream) {
+    if (!ctx || !in || !gk || !out || gk->ctx != ctx || batch < 1) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    if (!galois_ok(C, g)) return CKKS_EINVAL;
+    for (uint32_t i = 0; i < batch; ++i) {
+        if (!tuple_ok(&in[i], C.L) || in[i].n_polys != 2 || !in[i].ntt_form || !out[i].data ||
+            in[i].level != in[0].level || in[i].poly_stride != in[0].poly_stride)
+            return CKKS_EINVAL;
+    }
+    const int level = (int)in[0].level;
+    for (uint32_t i = 0; i < batch; ++i) {
+        if (out[i].poly_stride == 0) out[i].poly_stride = in[i].data == out[i].data ? in[i].poly_stride : level;
+        if ((int)out[i].poly_stride < level || out[i].poly_stride != out[0].poly_stride) return CKKS_EINVAL;
+    }
+    i64 is = batch_stride(in, batch), os = batch_stride(out, batch);
+    if (is < 0 || os < 0) return CKKS_EINVAL;
+    size_t need = rotate_ws_bytes(C, level, (int)batch);
+    if (!workspace || ws_bytes < need) return CKKS_ENOMEM;
+    cudaSetDevice(C.device);
+    cudaError_t err;
+    int rc = run_rotate_ws(C, (int)batch, level, g, tview(in[0], C.N, is), tview(out[0], C.N, os), gk->keys,
+                           workspace, ws_bytes, S(stream), err);
+    if (err != cudaSuccess || rc != 0) return cuda_fail(ctx, err == cudaSuccess ? cudaErrorUnknown : err);
+    for (uint32_t i = 0; i < batch; ++i) {
+        out[i].n_polys = 2;
+        out[i].level = (uint32_t)level;
+        out[i].ntt_form = 1;
+        out[i].scale = in[i].scale;
+    }
+    return CKKS_OK;
+}
+
+int ckks_rotate(ckks_context *ctx, const ckks_tuple *in, uint32_t g, const ckks_evk_set *gk, ckks_tuple *out,
+                void *workspace, size_t ws_bytes, void *stream) {
+    return ckks_rotate_batch(ctx, in, 1, g, gk, out, workspace, ws_bytes, stream);
+}
+
 int ckks_rescale_workspace_size(const ckks_context *ctx, uint32_t n_polys, uint32_t level, uint32_t mu,
                                 size_t *bytes) {
     if (!ctx || !bytes || mu < 1 || mu >= level || level > (uint32_t)ctx->c.L || n_polys < 1) return CKKS_EINVAL;
@@ -467,7 +596,7 @@ int ckks_counters(ckks_context *ctx, ckks_op_counters *out, int reset) {
 
 static const char *kClassNames[KC_COUNT] = {"ntt_fwd_cols", "ntt_fwd_blocks", "ntt_inv_blocks", "ntt_inv_cols",
                                             "tensor",       "bconv",          "key_mac",        "rs_chain",
-                                            "keys"};
+                                            "keys",         "automorphism"};
 
 int ckks_profile_enable(ckks_context *ctx, int enable) {
     if (!ctx) return CKKS_EINVAL;

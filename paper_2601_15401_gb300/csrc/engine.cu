@@ -518,6 +518,43 @@ int run_relin(const Context &C, int B, int n, int level, LimbView D, const u64 *
     return 0;
 }
 
+// Rotation (Galois automorphism sigma_g) with key switching back to s:
+// D = (sigma c0, 0, sigma c1), then the relinearisation steps with the one
+// Galois key in the place of ek_2 and ModDown finished in the NTT domain:
+// out = (sigma c0 + [P^-1 sigma(c1) gk_0], [P^-1 sigma(c1) gk_1]).
+static int run_rotate(const Context &C, int B, int level, uint32_t g, LimbView in, LimbView out, const u64 *keys,
+                      Ws &ws, cudaStream_t st, cudaError_t &err) {
+    const int N = C.N;
+    u64 *d = ws.take((size_t)B * 3 * level * N);
+    LimbView dv = view(d, (i64)3 * level * N, (i64)level * N);
+    err = cudaSuccess;
+    if (!ws.dry) {
+        AutoMap map{};
+        map.n_out = 3;
+        map.src[0] = 0;
+        map.src[1] = -1;
+        map.src[2] = 1;
+        err = launch_automorphism(C, in, dv, map, B, level, g, st);
+        if (err != cudaSuccess) return -5;
+    }
+    err = relin_core(C, ws, B, 2, level, dv, keys, 2, true, out, st);
+    return err == cudaSuccess ? 0 : -5;
+}
+
+size_t rotate_ws_bytes(const Context &C, int level, int B) {
+    Ws ws{nullptr, 0, 0, true};
+    LimbView v{};
+    cudaError_t err;
+    run_rotate(C, B, level, 1, v, v, nullptr, ws, 0, err);
+    return ws.off;
+}
+
+int run_rotate_ws(const Context &C, int B, int level, uint32_t g, LimbView in, LimbView out, const u64 *keys,
+                  void *wsp, size_t bytes, cudaStream_t st, cudaError_t &err) {
+    Ws ws{(char *)wsp, 0, bytes, false};
+    return run_rotate(C, B, level, g, in, out, keys, ws, st, err);
+}
+
 size_t rescale_ws_bytes(const Context &C, int polys, int level, int mu, int B) {
     Ws ws{nullptr, 0, 0, true};
     LimbView v{};

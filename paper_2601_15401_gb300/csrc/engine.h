@@ -9,6 +9,9 @@ size_t mul_k_ws_bytes(const Context &C, const Plan &P, int level, int B);
 size_t mul2_ws_bytes(const Context &C, int level, int B);
 size_t relin_ws_bytes(const Context &C, int n, int level, int B);
 size_t rescale_ws_bytes(const Context &C, int polys, int level, int mu, int B);
+size_t rotate_ws_bytes(const Context &C, int level, int B);
+int run_rotate_ws(const Context &C, int B, int level, uint32_t g, LimbView in, LimbView out, const u64 *keys,
+                  void *ws, size_t bytes, cudaStream_t st, cudaError_t &err);
 
 int run_mul_k_ws(const Context &C, const Plan &P, int level, int B, const LimbView *in, LimbView out,
                  const u64 *keys, int t_max, void *ws, size_t bytes, cudaStream_t st, cudaError_t &err);

@@ -72,6 +72,7 @@ enum KernelClass {
     KC_MAC,
     KC_RSCHAIN,
     KC_KEYS,
+    KC_AUTOMORPHISM,
     KC_COUNT
 };
 

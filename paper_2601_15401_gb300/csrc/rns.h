@@ -43,6 +43,13 @@ struct RsChainArgs {
     const Shoup *invq;
 };
 
+// Output polynomial p of an automorphism launch is sigma_g of input
+// polynomial src[p], or zero where src[p] < 0.
+struct AutoMap {
+    int n_out;
+    int src[16];
+};
+
 cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st);
 cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st);
 cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st);
@@ -50,6 +57,8 @@ cudaError_t launch_rschain(const Context &C, const RsChainArgs &A, cudaStream_t 
 cudaError_t launch_keyprep(const Context &C, u64 *keys, long long n_rows, cudaStream_t st);
 cudaError_t launch_signed_to_res(const Context &C, const long long *v, u64 *out, cudaStream_t st);
 cudaError_t launch_pointwise_mul(const Context &C, u64 *St, const u64 *S, cudaStream_t st);
+cudaError_t launch_automorphism(const Context &C, LimbView in, LimbView out, const AutoMap &map, int batch,
+                                int level, uint32_t g, cudaStream_t st);
 cudaError_t launch_add_limbs(const Context &C, LimbView dst, LimbView src, int batch, int polys, int level,
                              cudaStream_t st);
 cudaError_t launch_keygen(const Context &C, const u64 *S, const u64 *St, const u64 *E, const u64 *a, u64 *ek,

@@ -3,6 +3,7 @@ profiler captures (one kernel class at a time, a few GB on the device).
 
   python -m paper_2601_15401_gb300.microbench --op ntt --batch 16
   python -m paper_2601_15401_gb300.microbench --op mul_k --k 8 --batch 4
+  python -m paper_2601_15401_gb300.microbench --op rotate --batch 16
 
 Prints one JSON line: per kernel class, launches, average event time and
 achieved algorithmic GB/s (the library's timing hook).
@@ -20,7 +21,7 @@ def main():
     import synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2"], default="ntt")
+    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "rotate"], default="ntt")
     ap.add_argument("--log-n", type=int, default=16)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--k", type=int, default=8)
@@ -42,6 +43,26 @@ def main():
         def run():
             ctx.ntt(T)
             ctx.intt(T)
+    elif args.op == "rotate":
+        import numpy as np
+        g_el = ctx.galois_element(1)
+        gen = synth.rng(9, 0, stream=1)
+        s = torch.from_numpy(synth.ternary_secret(gen, N)).cuda()
+        e = torch.from_numpy(np.stack([synth.gaussian(gen, N) for _ in range(p.dnum)])).cuda()
+        a = synth.uniform_residues_torch(list(p.q) + list(p.p), (p.dnum,), N, 0x32, "cuda")
+        keys = torch.empty((p.dnum, 2, L + p.K, N), dtype=torch.uint64, device="cuda")
+        kws = torch.empty(ctx.keygen_workspace_size() // 8, dtype=torch.uint64, device="cuda")
+        ctx.keygen_galois(g_el, s, a, e, keys, kws)
+        del a, kws
+        gk = ctx.evk_set(2, keys)
+        inp = synth.uniform_residues_torch(p.q, (B, 2), N, 13, "cuda")
+        out = torch.empty((B, 2, L, N), dtype=torch.uint64, device="cuda")
+        cts = [G.Tuple(inp[b], 2, L, L) for b in range(B)]
+        outs = [G.Tuple(out[b], 2, L, L) for b in range(B)]
+        ws = torch.empty(ctx.rotate_workspace_size(L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
+
+        def run():
+            ctx.rotate_batch(cts, g_el, gk, outs, ws)
     else:
         t_max = max(args.k, 2)
         g = synth.rng(9, 0, stream=1)

@@ -223,6 +223,16 @@ def public_key_draw(params: Params, config: int):
 # ----------------------------------------------------------------------------
 # device-side draws for large throughput runs (same distributions)
 # ----------------------------------------------------------------------------
+def galois_key_draw(params: Params, config: int, g: int):
+    """Random inputs of the Galois key of g: a [dnum] x [L+K][N] uniform
+    residues (NTT domain), e [dnum] x [N] small errors."""
+    gen = rng(config, g, stream=5)
+    primes = list(params.q) + list(params.p)
+    a = [uniform_residues(gen, primes, params.N) for _ in range(params.dnum)]
+    e = [gaussian(gen, params.N) for _ in range(params.dnum)]
+    return a, e
+
+
 def uniform_residues_torch(primes, shape_prefix, N: int, seed: int, device):
     """Tensor [*shape_prefix][len(primes)][N] of uniform residues, limb j in
     [0, primes[j]), drawn on `device` with a seeded torch generator."""

@@ -433,3 +433,90 @@ def test_17_input_example():
 def test_6_input_depth_rule():
     assert plan.valid(plan.parse("(2,2,2)", 6), 6)
     assert not plan.valid(plan.parse("(5,1)|(3,2)", 6), 6)
+
+
+# --------------------------------------------------------------------------
+# Galois automorphisms and rotation
+# --------------------------------------------------------------------------
+def test_automorphism_closed_forms_and_homomorphism():
+    """sigma_g(X) = X^g (with X^N = -1), sigma_1 = id, sigma_g sigma_h =
+    sigma_{gh mod 2N}, and sigma_g(a b) = sigma_g(a) sigma_g(b)."""
+    N, q = 32, synth.prime_chain(50, 1)[0]
+    g0 = synth.rng(301)
+    x = np.zeros(N, dtype=np.uint64)
+    x[1] = 1
+    for g in (3, 5, 2 * N - 1, 41):
+        y = ckks.automorphism_coef(x, g, q)
+        want = np.zeros(N, dtype=np.uint64)
+        if g < N:
+            want[g] = 1
+        else:
+            want[g - N] = q - 1
+        assert np.array_equal(y, want)
+    a = synth.uniform_residues(g0, [q], N)[0]
+    b = synth.uniform_residues(g0, [q], N)[0]
+    assert np.array_equal(ckks.automorphism_coef(a, 1, q), a)
+    for g, h in ((5, 25), (3, 2 * N - 1), (7, 9)):
+        lhs = ckks.automorphism_coef(ckks.automorphism_coef(a, h, q), g, q)
+        assert np.array_equal(lhs, ckks.automorphism_coef(a, g * h % (2 * N), q))
+        ab = ring.negacyclic_mul(a, b, q)
+        assert np.array_equal(ckks.automorphism_coef(ab, g, q),
+                              ring.negacyclic_mul(ckks.automorphism_coef(a, g, q), ckks.automorphism_coef(b, g, q), q))
+    # the signed form agrees with the residue form
+    s = synth.ternary_secret(g0, N)
+    assert np.array_equal(ring.from_signed(ckks.automorphism_signed(s, 5), q),
+                          ckks.automorphism_coef(ring.from_signed(s, q), 5, q))
+    # in the NTT domain sigma_g permutes the limb, the same way for every prime
+    primes = synth.prime_chain(50, 2)
+    A = synth.uniform_residues(g0, primes, N)
+    B = ckks.automorphism_ntt(A, 5, primes)
+    perms = []
+    for j in range(2):
+        pos = {int(v): i for i, v in enumerate(A[j])}
+        perms.append([pos[int(v)] for v in B[j]])
+    assert perms[0] == perms[1] and sorted(perms[0]) == list(range(N))
+
+
+@pytest.mark.parametrize("r", [1, 3, -2, "conj"])
+def test_rotation_decodes_to_rotated_slots(r):
+    """Decrypt(rotate(Enc(z))) decodes to z rotated by r (g = 5^r) or to
+    conj(z) (g = 2N - 1), within 2^-20 (alpha = 1 digits, scale 2^50)."""
+    params = synth.make_params(8, [50] * 4, 1, 4)
+    ctx, km, keys, cts, zs = _encrypted_inputs(params, 2, 31, 2.0 ** 50)
+    N = params.N
+    g = 2 * N - 1 if r == "conj" else ckks.galois_element(r, N)
+    a, e = synth.galois_key_draw(params, 31, g)
+    gk = ckks.galois_keygen(ctx, km.s, a, e, g)
+    out = ckks.rotate(ctx, cts[0], g, gk)
+    assert out.level == cts[0].level
+    z = ckks.decode(N, ckks.decrypt(ctx, out.data, km.s), out.scale)
+    want = np.conj(zs[0]) if r == "conj" else np.roll(zs[0], -r)
+    assert np.abs(z - want).max() <= 2.0 ** -20
+    # the key of another element does not decrypt
+    g_bad = ckks.galois_element(r + 1 if r != "conj" else 1, N)
+    bad = ckks.rotate(ctx, cts[0], g, ckks.galois_keygen(ctx, km.s, a, e, g_bad))
+    zb = ckks.decode(N, ckks.decrypt(ctx, bad.data, km.s), bad.scale)
+    assert np.abs(zb - want).max() > 1.0
+
+
+def test_embedding_closed_forms():
+    """Canonical embedding: m = scale (constant 1) has every slot 1; m =
+    scale X has slot j = zeta_j; encoding inverts both; the per-slot and
+    per-coefficient forms agree with the vector forms."""
+    N, scale = 64, 2.0 ** 20
+    one = [int(scale)] + [0] * (N - 1)
+    x = [0, int(scale)] + [0] * (N - 2)
+    zeta = np.exp(1j * np.pi * np.array([pow(5, j, 2 * N) for j in range(N // 2)]) / N)
+    assert np.allclose(ckks.decode(N, one, scale), 1.0, atol=1e-12)
+    assert np.allclose(ckks.decode(N, x, scale), zeta, atol=1e-12)
+    assert ckks.encode(N, np.ones(N // 2, dtype=complex), scale) == one
+    assert ckks.encode(N, zeta, scale) == x
+    for j in (0, 5, N // 2 - 1):
+        assert abs(ckks.decode_slot(N, x, scale, j) - zeta[j]) < 1e-12
+    z = synth.unit_disk_slots(synth.rng(302), N // 2)
+    m = ckks.encode(N, z, scale)
+    for i in (0, 1, 17, N - 1):
+        assert abs(ckks.encode_coef(N, z, scale, i) - m[i]) <= 0.5 + 1e-6
+    dz = ckks.decode(N, m, scale)
+    for j in (0, 3, N // 2 - 1):
+        assert abs(ckks.decode_slot(N, m, scale, j) - dz[j]) < 1e-9
