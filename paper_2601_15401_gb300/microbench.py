@@ -21,7 +21,7 @@ def main():
     import synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "rotate"], default="ntt")
+    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "rotate", "encode", "decode"], default="ntt")
     ap.add_argument("--log-n", type=int, default=16)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--k", type=int, default=8)
@@ -43,6 +43,19 @@ def main():
         def run():
             ctx.ntt(T)
             ctx.intt(T)
+    elif args.op in ("encode", "decode"):
+        z = torch.randn((B, N // 2), dtype=torch.complex128, device="cuda") * 0.5
+        m = torch.empty((B, N), dtype=torch.int64, device="cuda")
+        mf = torch.empty((B, N), dtype=torch.float64, device="cuda")
+        ews = torch.empty(ctx.embed_workspace_size(B) // 8, dtype=torch.uint64, device="cuda")
+        ctx.encode(z, 2.0 ** 40, m, ews)
+        mf.copy_(m)
+
+        def run():
+            if args.op == "encode":
+                ctx.encode(z, 2.0 ** 40, m, ews)
+            else:
+                ctx.decode(mf, 2.0 ** 40, z, ews)
     elif args.op == "rotate":
         import numpy as np
         g_el = ctx.galois_element(1)
