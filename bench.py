@@ -258,6 +258,7 @@ def run_ours(args, rank, world, local_rank):
         st = dom[1]
         achieved = st["alg_bytes"] / (st["total_ms"] / 1e3) / 1e9
         traffic = None
+        busy = None
         try:
             ts = json.load(open(PROFILE_SUMMARY))
             ent = ts.get("kernels", {}).get(dom[0])
@@ -265,6 +266,7 @@ def run_ours(args, rank, world, local_rank):
                 # DRAM bytes per algorithmic byte from an ncu capture of this
                 # kernel class, scaled to this run's launches
                 traffic = round(ent["dram_bytes_per_alg_byte"] * st["alg_bytes"] / st["launches"])
+                busy = ent.get("fmaheavy_busy")
         except Exception:
             pass
         roofline = {"bound": "hbm", "kernel": dom[0], "achieved": round(achieved, 1), "peak": hbm_peak,
@@ -272,8 +274,10 @@ def run_ours(args, rank, world, local_rank):
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
                     "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
                     "avg_launch_us": st["total_ms"] * 1e3 / st["launches"],
-                    "limiter": "integer multiply (fmaheavy) pipe, not HBM: ncu shows it 55-83 % busy with "
-                               "math-pipe throttle as the top stall (profiles/)"}
+                    "fmaheavy_busy": busy,
+                    "limiter": "integer multiply (fmaheavy) pipe, not HBM: ncu shows it 54-71 % busy in the NTT "
+                               "phases, about 14 of its instructions per 64-bit Shoup product, DRAM traffic equal "
+                               "to the algorithmic bytes (profiles/ntt_phase_pipes_N65536_batch8.md, traffic.json)"}
     kernel_table = {n: {"launches": v["launches"] // args.steps, "ms_per_step": round(v["total_ms"] / args.steps, 3),
                         "share": round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4),
                         "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)}
