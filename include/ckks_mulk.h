@@ -151,6 +151,21 @@ int ckks_encrypt(ckks_context *ctx, const int64_t *m, const int64_t *v, const in
                  void *stream);
 int ckks_decrypt(ckks_context *ctx, const ckks_tuple *ct, const int64_t *s, double *out, void *workspace,
                  size_t ws_bytes, void *stream);
+/* Batched forms, one set of launches for many messages (the single calls
+ * above are batch 1). ckks_encrypt_batch: m, v, e_0, e_1 device int64
+ * [batch][N]; out[batch] evenly spaced tuples (one poly stride) at `level`.
+ * Workspace: ckks_encrypt_batch_workspace_size(level, batch) bytes (the
+ * messages are processed in chunks of up to 65535 / (4 level)).
+ * ckks_decrypt_batch: ct[batch] evenly spaced, same level and poly stride;
+ * out device double [batch][N]; batch <= 32767. Workspace:
+ * ckks_decrypt_batch_workspace_size(batch). Errors as for the single calls. */
+int ckks_encrypt_batch_workspace_size(const ckks_context *ctx, uint32_t level, uint32_t batch, size_t *bytes);
+int ckks_encrypt_batch(ckks_context *ctx, const int64_t *m, const int64_t *v, const int64_t *e0, const int64_t *e1,
+                       uint32_t batch, const uint64_t *pk, uint32_t level, ckks_tuple *out, void *workspace,
+                       size_t ws_bytes, void *stream);
+int ckks_decrypt_batch_workspace_size(const ckks_context *ctx, uint32_t batch, size_t *bytes);
+int ckks_decrypt_batch(ckks_context *ctx, const ckks_tuple *ct, uint32_t batch, const int64_t *s, double *out,
+                       void *workspace, size_t ws_bytes, void *stream);
 
 /* -------------------------------------------------------------- rotation
  * Slot rotation by a Galois automorphism sigma_g: a(X) -> a(X^g), g odd,

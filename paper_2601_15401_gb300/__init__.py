@@ -180,6 +180,39 @@ class Context:
         out.level, out.n_polys, out.ntt_form, out.poly_stride = o.level, o.n_polys, o.ntt_form, o.poly_stride
         return out
 
+    def encrypt_batch_workspace_size(self, level: int, batch: int) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ckks_encrypt_batch_workspace_size(self._h, level, batch, ctypes.byref(n)),
+               "ckks_encrypt_batch_workspace_size")
+        return n.value
+
+    def encrypt_batch(self, m, v, e0, e1, pk, level: int, outs, workspace, stream=None):
+        """m, v, e0, e1: int64 CUDA tensors [batch][N]; outs: evenly strided Tuples."""
+        B = len(outs)
+        oo = (_Tuple * B)(*[t.c() for t in outs])
+        _check(lib().ckks_encrypt_batch(self._h, m.data_ptr(), v.data_ptr(), e0.data_ptr(), e1.data_ptr(), B,
+                                        pk.data_ptr(), level, oo, workspace.data_ptr(),
+                                        workspace.numel() * workspace.element_size(), _stream(stream)),
+               "ckks_encrypt_batch")
+        for o, r in zip(outs, oo):
+            o.level, o.n_polys, o.ntt_form, o.poly_stride = r.level, r.n_polys, r.ntt_form, r.poly_stride
+        return outs
+
+    def decrypt_batch_workspace_size(self, batch: int) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ckks_decrypt_batch_workspace_size(self._h, batch, ctypes.byref(n)),
+               "ckks_decrypt_batch_workspace_size")
+        return n.value
+
+    def decrypt_batch(self, cts, s, out, workspace, stream=None):
+        """cts: evenly strided Tuples; out: float64 CUDA tensor [batch][N]."""
+        B = len(cts)
+        cc = (_Tuple * B)(*[t.c() for t in cts])
+        _check(lib().ckks_decrypt_batch(self._h, cc, B, s.data_ptr(), out.data_ptr(), workspace.data_ptr(),
+                                        workspace.numel() * workspace.element_size(), _stream(stream)),
+               "ckks_decrypt_batch")
+        return out
+
     def decrypt(self, ct: Tuple, s, out, workspace, stream=None):
         """out: float64 CUDA tensor [N] <- centred c_0 + c_1 s (two lowest limbs)."""
         c = ct.c()

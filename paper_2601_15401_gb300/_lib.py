@@ -38,6 +38,10 @@ SIGNATURES = {
     "ckks_rotate": [V, V, U32, V, V, V, SZ, V],
     "ckks_rotate_batch": [V, V, U32, U32, V, V, V, SZ, V],
     "ckks_encrypt_workspace_size": [V, V],
+    "ckks_encrypt_batch_workspace_size": [V, U32, U32, V],
+    "ckks_encrypt_batch": [V, V, V, V, V, U32, V, U32, V, V, SZ, V],
+    "ckks_decrypt_batch_workspace_size": [V, U32, V],
+    "ckks_decrypt_batch": [V, V, U32, V, V, V, SZ, V],
     "ckks_embed_workspace_size": [V, U32, V],
     "ckks_encode": [V, V, U32, D, V, V, SZ, V],
     "ckks_decode": [V, V, U32, D, V, V, SZ, V],

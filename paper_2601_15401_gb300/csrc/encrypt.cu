@@ -8,6 +8,8 @@
 //                                             centred, as a double
 // Everything is in the NTT domain except the small signed inputs, which are
 // reduced into every limb and transformed by the library's NTT.
+#include <algorithm>
+
 #include "../../include/ckks_mulk.h"
 #include "engine.h"
 #include "internal.h"
@@ -39,33 +41,13 @@ __global__ void pk_kernel(const u64 *S, const u64 *E, const u64 *a, u64 *pk, int
     pk[plane + gid] = a[gid];
 }
 
-// c0 = V pk0 + E0 + M, c1 = V pk1 + E1
-__global__ void enc_kernel(const u64 *V, const u64 *E0, const u64 *E1, const u64 *M, const u64 *pk, i64 pk_pstride,
-                           u64 *c0, u64 *c1, int limbs, int N, const ModQ *mods, const u64 *r2) {
-    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (i64)limbs * N) return;
-    const int x = (int)(gid / N);
-    const ModQ m = mods[x];
-    const u64 q = m.q;
-    c0[gid] = add_mod(add_mod(mulmod_full(V[gid], pk[gid], m, r2[x]), E0[gid], q), M[gid], q);
-    c1[gid] = add_mod(mulmod_full(V[gid], pk[pk_pstride + gid], m, r2[x]), E1[gid], q);
-}
-
-// P = C0 + C1 S over the lowest `limbs` limbs
-__global__ void dec_kernel(const u64 *c0, const u64 *c1, const u64 *S, u64 *P, int limbs, int N, const ModQ *mods,
-                           const u64 *r2) {
-    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (i64)limbs * N) return;
-    const int x = (int)(gid / N);
-    const ModQ m = mods[x];
-    P[gid] = add_mod(c0[gid], mulmod_full(c1[gid], S[gid], m, r2[x]), m.q);
-}
-
 // Garner lift of (x0 mod q0, x1 mod q1) to [0, q0 q1), centred, as double.
 __global__ void crt2_kernel(const u64 *P, double *out, int limbs, int N, u64 q0, u64 q1, Shoup q0inv_mod_q1,
                             u64 one_q1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    P += (i64)blockIdx.y * limbs * N;  // batch element
+    out += (i64)blockIdx.y * N;
     const u64 x0 = P[i];
     if (limbs == 1) {
         out[i] = x0 > q0 / 2 ? -(double)(q0 - x0) : (double)x0;
@@ -85,6 +67,51 @@ __global__ void crt2_kernel(const u64 *P, double *out, int limbs, int N, u64 q0,
     }
 }
 
+struct Src4 {
+    const i64 *p[4];
+};
+
+// signed [4][batch][N] (v, e0, e1, m) -> W[b][p][x][N] residues, x < level;
+// blockIdx.y = b * 4 + p
+__global__ void signed4_kernel(Src4 src, u64 *W, int level, int N, const ModQ *mods) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (i64)level * N) return;
+    const int b = blockIdx.y / 4, p = blockIdx.y % 4;
+    const int x = (int)(gid / N), i = (int)(gid % N);
+    const i64 v = src.p[p][(i64)b * N + i];
+    const u64 q = mods[x].q;
+    const u64 r = v >= 0 ? ((u64)v) % q : ((u64)(-v)) % q;
+    W[((i64)blockIdx.y * level) * N + gid] = (v >= 0 || r == 0) ? r : q - r;
+}
+
+// c0 = V pk0 + E0 + M, c1 = V pk1 + E1 for every batch element (blockIdx.y)
+__global__ void enc_batch_kernel(const u64 *W, const u64 *pk, i64 pk_pstride, u64 *out, i64 out_bstride,
+                                 i64 out_pstride, int level, int N, const ModQ *mods, const u64 *r2) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (i64)level * N) return;
+    const int b = blockIdx.y;
+    const int x = (int)(gid / N);
+    const ModQ m = mods[x];
+    const u64 q = m.q;
+    const i64 plane = (i64)level * N;
+    const u64 *w = W + (i64)b * 4 * plane + gid;  // V, E0, E1, M
+    u64 *c0 = out + (i64)b * out_bstride + gid, *c1 = c0 + out_pstride;
+    *c0 = add_mod(add_mod(mulmod_full(w[0], pk[gid], m, r2[x]), w[plane], q), w[3 * plane], q);
+    *c1 = add_mod(mulmod_full(w[0], pk[pk_pstride + gid], m, r2[x]), w[2 * plane], q);
+}
+
+// P[b][x] = C0 + C1 S over the lowest `limbs` limbs of every batch element
+__global__ void dec_batch_kernel(const u64 *ct, i64 bstride, i64 pstride, const u64 *S, u64 *P, int limbs, int N,
+                                 const ModQ *mods, const u64 *r2) {
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (i64)limbs * N) return;
+    const int b = blockIdx.y;
+    const int x = (int)(gid / N);
+    const ModQ m = mods[x];
+    const u64 *c0 = ct + (i64)b * bstride + gid;
+    P[(i64)b * limbs * N + gid] = add_mod(c0[0], mulmod_full(c0[pstride], S[gid], m, r2[x]), m.q);
+}
+
 unsigned blocks(i64 n) { return (unsigned)((n + kThr - 1) / kThr); }
 
 // NTT of `limbs` limbs in place (prime index = limb index)
@@ -102,6 +129,23 @@ u64 host_inv(u64 a, u64 q) {
         e >>= 1;
     }
     return (u64)r;
+}
+
+size_t enc_batch_ws(const Context &C, uint32_t level, uint32_t batch) {
+    const uint32_t chunk = std::min<uint32_t>(16383u, 65535u / (4u * level));
+    return (size_t)std::min(batch, chunk) * 4 * level * C.N * sizeof(u64);
+}
+
+size_t dec_batch_ws(const Context &C, uint32_t batch) {
+    return ((size_t)(C.L + C.K) * C.N + (size_t)batch * 2 * C.N) * sizeof(u64);
+}
+
+// evenly spaced tuple array: batch stride in elements, -1 if not
+i64 spacing(const ckks_tuple *t, uint32_t batch) {
+    const i64 bs = batch > 1 ? (i64)(t[1].data - t[0].data) : 0;
+    for (uint32_t b = 0; b < batch; ++b)
+        if (t[b].data != t[0].data + b * bs) return -1;
+    return bs;
 }
 
 }  // namespace
@@ -141,71 +185,104 @@ int ckks_public_key(ckks_context *ctx, const int64_t *s, const uint64_t *a, cons
     return CKKS_OK;
 }
 
-int ckks_encrypt(ckks_context *ctx, const int64_t *m, const int64_t *v, const int64_t *e0, const int64_t *e1,
-                 const uint64_t *pk, uint32_t level, ckks_tuple *out, void *workspace, size_t ws_bytes,
-                 void *stream) {
-    if (!ctx || !m || !v || !e0 || !e1 || !pk || !out || !out->data || !workspace) return CKKS_EINVAL;
+int ckks_encrypt_batch_workspace_size(const ckks_context *ctx, uint32_t level, uint32_t batch, size_t *bytes) {
+    if (!ctx || !bytes || batch < 1) return CKKS_EINVAL;
+    if (level < 1 || level > (uint32_t)ctx->c.L) return CKKS_ELEVEL;
+    *bytes = enc_batch_ws(ctx->c, level, batch);
+    return CKKS_OK;
+}
+
+int ckks_encrypt_batch(ckks_context *ctx, const int64_t *m, const int64_t *v, const int64_t *e0, const int64_t *e1,
+                       uint32_t batch, const uint64_t *pk, uint32_t level, ckks_tuple *out, void *workspace,
+                       size_t ws_bytes, void *stream) {
+    if (!ctx || !m || !v || !e0 || !e1 || !pk || !out || !workspace || batch < 1) return CKKS_EINVAL;
     const Context &C = ctx->c;
     if (level < 1 || level > (uint32_t)C.L) return CKKS_ELEVEL;
-    if (out->poly_stride == 0) out->poly_stride = level;
-    if (out->poly_stride < level) return CKKS_EINVAL;
-    size_t need;
-    ckks_encrypt_workspace_size(ctx, &need);
-    if (ws_bytes < need) return CKKS_ENOMEM;
+    for (uint32_t b = 0; b < batch; ++b) {
+        if (!out[b].data) return CKKS_EINVAL;
+        if (out[b].poly_stride == 0) out[b].poly_stride = level;
+        if (out[b].poly_stride < level || out[b].poly_stride != out[0].poly_stride) return CKKS_EINVAL;
+    }
+    const i64 os = spacing(out, batch);
+    if (os < 0) return CKKS_EINVAL;
+    if (ws_bytes < enc_batch_ws(C, level, batch)) return CKKS_ENOMEM;
     cudaSetDevice(C.device);
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t plane = (size_t)(C.L + C.K) * C.N;
-    u64 *V = (u64 *)workspace, *E0 = V + plane, *E1 = E0 + plane, *M = E1 + plane;
-    const int64_t *src[4] = {v, e0, e1, m};
-    u64 *dst[4] = {V, E0, E1, M};
+    const uint32_t chunk = std::min<uint32_t>(16383u, 65535u / (4u * level));
+    const i64 N = C.N, ps = (i64)out[0].poly_stride * N;
+    u64 *W = (u64 *)workspace;
     cudaError_t err = cudaSuccess;
-    for (int i = 0; i < 4 && err == cudaSuccess; ++i) {
-        err = launch_signed_to_res(C, (const long long *)src[i], dst[i], st);
-        if (err == cudaSuccess) err = ntt_limbs(C, dst[i], (int)level, st);
-    }
-    if (err == cudaSuccess) {
-        u64 *c0 = (u64 *)out->data, *c1 = c0 + (size_t)out->poly_stride * C.N;
+    for (uint32_t b0 = 0; b0 < batch && err == cudaSuccess; b0 += chunk) {
+        const uint32_t cb = std::min(chunk, batch - b0);
+        Src4 src{{(const i64 *)v + b0 * N, (const i64 *)e0 + b0 * N, (const i64 *)e1 + b0 * N,
+                  (const i64 *)m + b0 * N}};
         count_kernel(C);
-        enc_kernel<<<blocks((i64)level * C.N), kThr, 0, st>>>(V, E0, E1, M, (const u64 *)pk, (i64)C.L * C.N, c0, c1,
-                                                              (int)level, C.N, C.d_mods, C.d_r2);
+        signed4_kernel<<<dim3(blocks((i64)level * N), cb * 4), kThr, 0, st>>>(src, W, (int)level, C.N, C.d_mods);
         err = cudaGetLastError();
+        if (err == cudaSuccess) {
+            LimbView w{W, 4 * (i64)level * N, (i64)level * N};
+            err = transform_plain(C, true, (int)cb, 4, (int)level, w, w, st);
+        }
+        if (err == cudaSuccess) {
+            count_kernel(C);
+            enc_batch_kernel<<<dim3(blocks((i64)level * N), cb), kThr, 0, st>>>(
+                W, (const u64 *)pk, (i64)C.L * N, (u64 *)out[b0].data, os, ps, (int)level, C.N, C.d_mods, C.d_r2);
+            err = cudaGetLastError();
+        }
     }
     if (err != cudaSuccess) {
         const_cast<Context &>(C).sticky.store((int)err);
         return CKKS_ECUDA;
     }
-    out->n_polys = 2;
-    out->level = level;
-    out->ntt_form = 1;
+    for (uint32_t b = 0; b < batch; ++b) {
+        out[b].n_polys = 2;
+        out[b].level = level;
+        out[b].ntt_form = 1;
+    }
     return CKKS_OK;
 }
 
-int ckks_decrypt(ckks_context *ctx, const ckks_tuple *ct, const int64_t *s, double *out, void *workspace,
-                 size_t ws_bytes, void *stream) {
-    if (!ctx || !ct || !ct->data || !s || !out || !workspace) return CKKS_EINVAL;
+int ckks_encrypt(ckks_context *ctx, const int64_t *m, const int64_t *v, const int64_t *e0, const int64_t *e1,
+                 const uint64_t *pk, uint32_t level, ckks_tuple *out, void *workspace, size_t ws_bytes,
+                 void *stream) {
+    return ckks_encrypt_batch(ctx, m, v, e0, e1, 1, pk, level, out, workspace, ws_bytes, stream);
+}
+
+int ckks_decrypt_batch_workspace_size(const ckks_context *ctx, uint32_t batch, size_t *bytes) {
+    if (!ctx || !bytes || batch < 1) return CKKS_EINVAL;
+    *bytes = dec_batch_ws(ctx->c, batch);
+    return CKKS_OK;
+}
+
+int ckks_decrypt_batch(ckks_context *ctx, const ckks_tuple *ct, uint32_t batch, const int64_t *s, double *out,
+                       void *workspace, size_t ws_bytes, void *stream) {
+    if (!ctx || !ct || !s || !out || !workspace || batch < 1 || batch > 32767) return CKKS_EINVAL;
     const Context &C = ctx->c;
-    if (ct->n_polys != 2 || !ct->ntt_form || ct->level < 1 || ct->level > (uint32_t)C.L ||
-        ct->poly_stride < ct->level)
-        return CKKS_EINVAL;
-    size_t need;
-    ckks_encrypt_workspace_size(ctx, &need);
-    if (ws_bytes < need) return CKKS_ENOMEM;
+    for (uint32_t b = 0; b < batch; ++b) {
+        if (!ct[b].data || ct[b].n_polys != 2 || !ct[b].ntt_form || ct[b].level < 1 ||
+            ct[b].level > (uint32_t)C.L || ct[b].poly_stride < ct[b].level || ct[b].level != ct[0].level ||
+            ct[b].poly_stride != ct[0].poly_stride)
+            return CKKS_EINVAL;
+    }
+    const i64 cs = spacing(ct, batch);
+    if (cs < 0) return CKKS_EINVAL;
+    if (ws_bytes < dec_batch_ws(C, batch)) return CKKS_ENOMEM;
     cudaSetDevice(C.device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int limbs = ct->level >= 2 ? 2 : 1;
-    const size_t plane = (size_t)(C.L + C.K) * C.N;
-    u64 *S = (u64 *)workspace, *P = S + plane;
+    const int limbs = ct[0].level >= 2 ? 2 : 1;
+    const i64 N = C.N;
+    u64 *S = (u64 *)workspace, *P = S + (size_t)(C.L + C.K) * N;
     cudaError_t err = launch_signed_to_res(C, (const long long *)s, S, st);
     if (err == cudaSuccess) err = ntt_limbs(C, S, limbs, st);
     if (err == cudaSuccess) {
-        const u64 *c0 = (const u64 *)ct->data, *c1 = c0 + (size_t)ct->poly_stride * C.N;
         count_kernel(C);
-        dec_kernel<<<blocks((i64)limbs * C.N), kThr, 0, st>>>(c0, c1, S, P, limbs, C.N, C.d_mods, C.d_r2);
+        dec_batch_kernel<<<dim3(blocks((i64)limbs * N), batch), kThr, 0, st>>>(
+            (const u64 *)ct[0].data, cs, (i64)ct[0].poly_stride * N, S, P, limbs, C.N, C.d_mods, C.d_r2);
         err = cudaGetLastError();
     }
     if (err == cudaSuccess) {
-        LimbView v{P, 0, (i64)limbs * C.N};
-        err = transform_plain(C, false, 1, 1, limbs, v, v, st);
+        LimbView v{P, (i64)limbs * N, (i64)limbs * N};
+        err = transform_plain(C, false, (int)batch, 1, limbs, v, v, st);
     }
     if (err == cudaSuccess) {
         const u64 q0 = C.primes[0], q1 = limbs > 1 ? C.primes[1] : 1;
@@ -217,7 +294,7 @@ int ckks_decrypt(ckks_context *ctx, const ckks_tuple *ct, const int64_t *s, doub
             one_q1 = (u64)(((unsigned __int128)1 << 64) / q1);
         }
         count_kernel(C);
-        crt2_kernel<<<blocks(C.N), kThr, 0, st>>>(P, out, limbs, C.N, q0, q1, inv, one_q1);
+        crt2_kernel<<<dim3(blocks(N), batch), kThr, 0, st>>>(P, out, limbs, C.N, q0, q1, inv, one_q1);
         err = cudaGetLastError();
     }
     if (err != cudaSuccess) {
@@ -225,6 +302,11 @@ int ckks_decrypt(ckks_context *ctx, const ckks_tuple *ct, const int64_t *s, doub
         return CKKS_ECUDA;
     }
     return CKKS_OK;
+}
+
+int ckks_decrypt(ckks_context *ctx, const ckks_tuple *ct, const int64_t *s, double *out, void *workspace,
+                 size_t ws_bytes, void *stream) {
+    return ckks_decrypt_batch(ctx, ct, 1, s, out, workspace, ws_bytes, stream);
 }
 
 }  // extern "C"

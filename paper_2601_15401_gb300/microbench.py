@@ -4,6 +4,11 @@ profiler captures (one kernel class at a time, a few GB on the device).
   python -m paper_2601_15401_gb300.microbench --op ntt --batch 16
   python -m paper_2601_15401_gb300.microbench --op mul_k --k 8 --batch 4
   python -m paper_2601_15401_gb300.microbench --op rotate --batch 16
+  python -m paper_2601_15401_gb300.microbench --op precision --batch 4 --secret-h 64
+
+--op precision prints, per k = 2..12, the largest slot error of the device
+round trip encode -> encrypt -> k-input product -> decrypt -> decode
+against the FP64 product of the slot vectors (no timing).
 
 Prints one JSON line: per kernel class, launches, average event time and
 achieved algorithmic GB/s (the library's timing hook).
@@ -21,7 +26,7 @@ def main():
     import synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "rotate", "encode", "decode"], default="ntt")
+    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "rotate", "encode", "decode", "precision"], default="ntt")
     ap.add_argument("--log-n", type=int, default=16)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--k", type=int, default=8)
@@ -29,7 +34,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--tune", action="append", default=[], help="key=value library tunable")
     ap.add_argument("--partition", default=None, help="partition text for --op mul_k (default Table II)")
+    ap.add_argument("--secret-h", type=int, default=0, help="--op precision: Hamming weight of s (0: uniform)")
+    ap.add_argument("--scale-bits", type=int, default=50, help="--op precision: log2 of the encoding scale")
     args = ap.parse_args()
+    if args.op == "precision":
+        return precision(args)
     p = synth.params_large(log_n=args.log_n)
     ctx = G.Context.from_params(p)
     L, N, B = p.L, p.N, args.batch
@@ -128,6 +137,56 @@ def main():
         "ms_per_rep": round(e0.elapsed_time(e1) / args.reps, 4), "counters_per_rep": {n: v // args.reps for n, v in ctx.counters().items()},
         "kernels": {n: {"launches": v["launches"], "avg_us": round(v["total_ms"] * 1e3 / v["launches"], 2),
                         "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)} for n, v in prof.items()}}))
+
+
+def precision(args):
+    import numpy as np
+    import torch
+
+    import paper_2601_15401_gb300 as G
+    import synth
+    from .serve import build_gpu_state, build_plaintext_keys
+    h = args.secret_h or None
+    contexts, _ = build_gpu_state((args.log_n,), pool_size=1, secret_h=h)
+    keys = build_plaintext_keys(contexts, secret_h=h)
+    ctx, evk = contexts[args.log_n]
+    s, pk = keys[args.log_n]
+    N, L, B, scale = ctx.N, ctx.L, args.batch, 2.0 ** args.scale_bits
+    rows = {}
+    for k in range(2, 13):
+        zs = np.stack([synth.unit_disk_slots(synth.rng(11, k * 100 + i, stream=6), N // 2) for i in range(B * k)])
+        ews = torch.empty(ctx.embed_workspace_size(B * k) // 8 + 1, dtype=torch.uint64, device="cuda")
+        m = torch.empty((B * k, N), dtype=torch.int64, device="cuda")
+        ctx.encode(torch.from_numpy(zs).cuda(), scale, m, ews)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1000 + k)
+        v = torch.randint(-1, 2, (B * k, N), generator=g, device="cuda", dtype=torch.int64)
+        e = (torch.randn((2, B * k, N), generator=g, device="cuda", dtype=torch.float64) * synth.SIGMA).round()
+        e = e.clamp_(-synth.ERR_CLIP, synth.ERR_CLIP).to(torch.int64)
+        ct = torch.empty((B * k, 2, L, N), dtype=torch.uint64, device="cuda")
+        cts = [G.Tuple(ct[i], 2, L, L, scale=scale) for i in range(B * k)]
+        ws = torch.empty(ctx.encrypt_batch_workspace_size(L, B * k) // 8 + 1, dtype=torch.uint64, device="cuda")
+        ctx.encrypt_batch(m, v, e[0].contiguous(), e[1].contiguous(), pk, L, cts, ws)
+        for t in cts:
+            t.scale = scale
+        depth = ctx.plan_describe(k)["depth"]
+        out = torch.empty((B, 2, L - depth, N), dtype=torch.uint64, device="cuda")
+        outs = [G.Tuple(out[b], 2, L - depth, L - depth) for b in range(B)]
+        mws = torch.empty(ctx.workspace_size(k, L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
+        ctx.mul_k_batch([cts[b * k:(b + 1) * k] for b in range(B)], evk, outs, mws)
+        dec = torch.empty((B, N), dtype=torch.float64, device="cuda")
+        dws = torch.empty(ctx.decrypt_batch_workspace_size(B) // 8 + 1, dtype=torch.uint64, device="cuda")
+        ctx.decrypt_batch(outs, s, dec, dws)
+        zo = torch.empty((B, N // 2), dtype=torch.complex128, device="cuda")
+        ctx.decode(dec, outs[0].scale, zo, ews)
+        want = np.prod(zs.reshape(B, k, N // 2), axis=1)
+        err = float(np.abs(zo.cpu().numpy() - want).max())
+        rows[k] = {"max_abs_err": err, "log2": round(float(np.log2(err)), 1) if err > 0 else None}
+        del ct, ws, mws, out, dec, ews, m
+        torch.cuda.empty_cache()
+    print(json.dumps({"op": "precision", "log_n": args.log_n, "L": L, "K": ctx.K, "dnum": ctx.dnum,
+                      "scale_bits": args.scale_bits, "batch": B,
+                      "secret": f"Hamming weight {h}" if h else "uniform ternary", "per_k": rows}))
 
 
 if __name__ == "__main__":

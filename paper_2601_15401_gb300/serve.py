@@ -41,6 +41,8 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     error: str | None = None
+    slots: object = None     # plaintext requests: [k][N/2] complex slot vectors (cts unused)
+    seed: int = 0            # plaintext requests: seed of the encryption noise
 
     @property
     def shape(self):
@@ -255,6 +257,115 @@ class GpuBackend:
         b.handle = None
 
 
+class PlaintextBackend(GpuBackend):
+    """Plaintext in, plaintext out: a batch of requests carrying slot vectors
+    runs encode -> encrypt (batched) -> k-input product -> decrypt (batched)
+    -> decode on its stream, every step in the library. This is the pipeline
+    of the party that holds the secret (e.g. a client batching its own
+    products); the encryption noise of a request is drawn from its own seed,
+    so its result does not depend on the batch it lands in.
+
+    keys: {log_n: (s, pk)} device secret (int64 [N]) and public key [2][L][N]."""
+
+    def __init__(self, contexts, keys, scale: float = 2.0 ** 50, **kw):
+        super().__init__(contexts, pools={}, **kw)
+        self.keys = keys
+        self.scale = scale
+
+    def footprint(self, shape, n: int) -> int:
+        key = ("pt", shape, n)
+        if key not in self._fp_cache:
+            log_n, k, level, part = shape
+            ctx, _ = self.contexts[log_n]
+            N = ctx.N
+            depth = ctx.plan_describe(k, part)["depth"]
+            cts = n * k * 2 * level * N * 8 + n * 2 * (level - depth) * N * 8
+            plain = n * k * N * (16 + 8 + 3 * 8) + n * N * (8 + 16)
+            enc_ws = ctx.encrypt_batch_workspace_size(level, n * k) + ctx.decrypt_batch_workspace_size(n)
+            emb_ws = ctx.embed_workspace_size(n * k)
+            self._fp_cache[key] = cts + plain + enc_ws + emb_ws
+        return self._fp_cache[key]
+
+    def _noise(self, r: Request, N: int, k: int):
+        import synth
+        torch = self.torch
+        g = torch.Generator(device="cuda")
+        g.manual_seed(int(r.seed))
+        v = torch.randint(-1, 2, (k, N), generator=g, device="cuda", dtype=torch.int64)
+        e = torch.randn((2, k, N), generator=g, device="cuda", dtype=torch.float64) * synth.SIGMA
+        e = e.round().clamp_(-synth.ERR_CLIP, synth.ERR_CLIP).to(torch.int64)
+        return v, e[0], e[1]
+
+    def launch(self, b: Batch):
+        torch = self.torch
+        import numpy as np
+        from . import Tuple
+        log_n, k, level, part = b.shape
+        ctx, evk = self.contexts[log_n]
+        s, pk = self.keys[log_n]
+        N = ctx.N
+        depth = ctx.plan_describe(k, part)["depth"]
+        st = self.streams[b.stream]
+        n = len(b.reqs)
+        with torch.cuda.stream(st):
+            z = torch.from_numpy(np.ascontiguousarray(np.concatenate([r.slots for r in b.reqs]), dtype=np.complex128))
+            z = z.pin_memory().to("cuda", non_blocking=True)                      # [n k][N/2]
+            emb_ws = torch.empty(ctx.embed_workspace_size(n * k) // 8 + 1, dtype=torch.uint64, device="cuda")
+            m = torch.empty((n * k, N), dtype=torch.int64, device="cuda")
+            ctx.encode(z, self.scale, m, emb_ws, stream=st)
+            noise = [self._noise(r, N, k) for r in b.reqs]
+            v = torch.cat([x[0] for x in noise])
+            e0 = torch.cat([x[1] for x in noise])
+            e1 = torch.cat([x[2] for x in noise])
+            ct = torch.empty((n * k, 2, level, N), dtype=torch.uint64, device="cuda")
+            cts = [Tuple(ct[i], 2, level, level, scale=self.scale) for i in range(n * k)]
+            enc_ws = torch.empty(ctx.encrypt_batch_workspace_size(level, n * k) // 8 + 1, dtype=torch.uint64,
+                                 device="cuda")
+            ctx.encrypt_batch(m, v, e0, e1, pk, level, cts, enc_ws, stream=st)
+            for t in cts:
+                t.scale = self.scale
+            out = torch.empty((n, 2, level - depth, N), dtype=torch.uint64, device="cuda")
+            outs = [Tuple(out[i], 2, level - depth, level - depth) for i in range(n)]
+            tup = [cts[i * k:(i + 1) * k] for i in range(n)]
+            ctx.mul_k_batch(tup, evk, outs, self.ws[b.stream], partition=part, stream=st)
+            dec = torch.empty((n, N), dtype=torch.float64, device="cuda")
+            dec_ws = torch.empty(ctx.decrypt_batch_workspace_size(n) // 8 + 1, dtype=torch.uint64, device="cuda")
+            ctx.decrypt_batch(outs, s, dec, dec_ws, stream=st)
+            zo = torch.empty((n, N // 2), dtype=torch.complex128, device="cuda")
+            ctx.decode(dec, outs[0].scale, zo, emb_ws, stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return (ev, zo, (z, m, v, e0, e1, ct, out, dec, emb_ws, enc_ws, dec_ws))
+
+    def finish(self, b: Batch):
+        if self.keep_results:
+            zo = b.handle[1].cpu().numpy()
+            for i, r in enumerate(b.reqs):
+                self.results[r.rid] = zo[i]
+        b.handle = None
+
+
+def build_plaintext_keys(contexts, device=0, secret_h=None):
+    """Public key of each context's secret (the secret of build_gpu_state,
+    with the same secret_h)."""
+    import torch
+
+    import synth
+    keys = {}
+    for log_n, (ctx, _) in contexts.items():
+        N = ctx.N
+        g = synth.rng(5, log_n, stream=1)
+        s = torch.from_numpy(synth.secret(g, N, secret_h)).cuda()
+        pa = synth.uniform_residues_torch(list(ctx.q), (), N, 0x7A + log_n, "cuda")
+        pe = torch.from_numpy(synth.gaussian(synth.rng(6, log_n, stream=4), N)).cuda()
+        pk = torch.empty((2, ctx.L, N), dtype=torch.uint64, device="cuda")
+        ws = torch.empty(ctx.encrypt_workspace_size() // 8, dtype=torch.uint64, device="cuda")
+        ctx.public_key(s, pa, pe, pk, ws)
+        keys[log_n] = (s, pk)
+    torch.cuda.synchronize()
+    return keys
+
+
 def poisson_arrivals(rate: float, seconds: float, rng) -> list[float]:
     t, out = 0.0, []
     while True:
@@ -313,8 +424,30 @@ def mixed_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size=64,
     return reqs
 
 
-def build_gpu_state(log_ns, L=24, K=8, dnum=3, t_max=12, pool_size=64, device=0):
-    """Contexts, resident keys (generated on the device) and ciphertext pools."""
+def plaintext_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size=16, k_range=(2, 12)):
+    """The mixed workload with slot vectors instead of pool ciphertexts: each
+    request multiplies k slot vectors taken from a per-N pool of unit-disk
+    vectors; its encryption noise is seeded by the request."""
+    import numpy as np
+
+    import synth
+    g = np.random.default_rng(seed)
+    pools = {log_n: [synth.unit_disk_slots(synth.rng(7, log_n * 100 + i, stream=6), 1 << (log_n - 1))
+                     for i in range(pool_size)] for log_n in log_ns}
+    reqs = []
+    for i, t in enumerate(poisson_arrivals(rate, seconds, g)):
+        k = int(g.integers(k_range[0], k_range[1] + 1))
+        log_n = int(g.choice(log_ns))
+        level = int(g.integers(k, L + 1))
+        idx = [int(x) for x in g.integers(0, pool_size, size=k)]
+        reqs.append(Request(i, log_n, k, level, tuple(idx), arrival=t,
+                            slots=np.stack([pools[log_n][j] for j in idx]), seed=seed * 1000003 + i))
+    return reqs
+
+
+def build_gpu_state(log_ns, L=24, K=8, dnum=3, t_max=12, pool_size=64, device=0, secret_h=None):
+    """Contexts, resident keys (generated on the device) and ciphertext pools.
+    secret_h: Hamming weight of the secret (None: uniform ternary)."""
     import numpy as np
     import torch
 
@@ -327,7 +460,7 @@ def build_gpu_state(log_ns, L=24, K=8, dnum=3, t_max=12, pool_size=64, device=0)
         ctx = Context.from_params(params, device=device)
         g = synth.rng(5, log_n, stream=1)
         N = params.N
-        s = torch.from_numpy(synth.ternary_secret(g, N)).cuda()
+        s = torch.from_numpy(synth.secret(g, N, secret_h)).cuda()
         e = torch.from_numpy(np.stack([[synth.gaussian(g, N) for _ in range(dnum)] for _ in range(t_max - 1)])).cuda()
         a = synth.uniform_residues_torch(list(params.q) + list(params.p), (t_max - 1, dnum), N, 0x5E + log_n, "cuda")
         keys = torch.empty((t_max - 1, dnum, 2, L + K, N), dtype=torch.uint64, device="cuda")
@@ -351,23 +484,47 @@ def main():
     ap.add_argument("--ws-gb", type=float, default=6.0)
     ap.add_argument("--log-ns", default="14,15,16")
     ap.add_argument("--seed", type=int, default=2026)
+    ap.add_argument("--secret-h", type=int, default=0,
+                    help="Hamming weight of the secret (0: uniform ternary)")
+    ap.add_argument("--plaintext", action="store_true",
+                    help="requests carry slot vectors: encode, encrypt, multiply, decrypt, decode on the device")
+    ap.add_argument("--k-max", type=int, default=12)
     args = ap.parse_args()
     log_ns = tuple(int(x) for x in args.log_ns.split(","))
-    contexts, pools = build_gpu_state(log_ns)
-    be = GpuBackend(contexts, pools, n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)))
+    h = args.secret_h or None
+    contexts, pools = build_gpu_state(log_ns, pool_size=1 if args.plaintext else 64, secret_h=h)
+    if args.plaintext:
+        be = PlaintextBackend(contexts, build_plaintext_keys(contexts, secret_h=h), n_streams=args.streams,
+                              ws_bytes=int(args.ws_gb * (1 << 30)), keep_results=True)
+
+        def make(rate, seconds, seed, lns):
+            return plaintext_requests(rate, seconds, seed, lns, k_range=(2, args.k_max))
+    else:
+        be = GpuBackend(contexts, pools, n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)))
+
+        def make(rate, seconds, seed, lns):
+            return mixed_requests(rate, seconds, seed, lns, k_range=(2, args.k_max))
     # the cap covers everything on the device: keys, pools, tables and stream
     # workspaces are resident; batches are admitted within what is left
     resident = be.resident_bytes()
     budget = int(args.cap_gb * 1e9) - resident
     if budget <= 0:
         raise SystemExit(f"resident state ({resident / 1e9:.1f} GB) exceeds the cap")
-    warm = mixed_requests(200.0, 0.2, args.seed + 1, log_ns)
+    warm = make(200.0, 0.2, args.seed + 1, log_ns)
     run_open_loop(Scheduler(be, budget, args.max_batch), warm)
-    reqs = mixed_requests(args.rate, args.seconds, args.seed, log_ns)
+    reqs = make(args.rate, args.seconds, args.seed, log_ns)
     sched = Scheduler(be, budget, args.max_batch)
     wall = run_open_loop(sched, reqs, timeout=args.seconds * 20 + 120)
     stats = latency_stats(sched.completed)
-    sizes = {}
+    extra = {}
+    if args.plaintext:
+        import numpy as np
+        err = {}
+        for r in sched.completed:
+            e = float(np.abs(be.results[r.rid] - np.prod(r.slots, axis=0)).max())
+            err[r.k] = max(err.get(r.k, 0.0), e)
+        extra = {"mode": "plaintext in / plaintext out", "max_abs_slot_error_per_k": dict(sorted(err.items())),
+                 "secret": f"Hamming weight {h}" if h else "uniform ternary"}
     print(json.dumps({"metric": "served k-input ct-mults/s (Poisson arrivals, mixed k, N, level)",
                       "offered_rate": args.rate, "seconds": args.seconds, "requests": len(reqs),
                       "completed": len(sched.completed), "wall_s": round(wall, 3),
@@ -375,7 +532,7 @@ def main():
                       "batches": sched.admitted_batches, "mean_batch": round(len(reqs) / max(1, sched.admitted_batches), 2),
                       "streams": args.streams, "max_batch": args.max_batch, "cap_gb": args.cap_gb,
                       "resident_gb": round(resident / 1e9, 2), "peak_allocated_gb": round(
-                          __import__("torch").cuda.max_memory_allocated() / 1e9, 2)}))
+                          __import__("torch").cuda.max_memory_allocated() / 1e9, 2), **extra}))
 
 
 if __name__ == "__main__":

@@ -145,6 +145,11 @@ def ternary_secret(g: np.random.Generator, N: int) -> np.ndarray:
     return g.integers(-1, 2, size=N, dtype=np.int64)
 
 
+def secret(g: np.random.Generator, N: int, h: int | None = None) -> np.ndarray:
+    """The secret: uniform ternary (h None), or ternary of Hamming weight h."""
+    return ternary_secret(g, N) if not h else ternary_weight(g, N, h)
+
+
 def ternary_weight(g: np.random.Generator, N: int, h: int) -> np.ndarray:
     v = np.zeros(N, dtype=np.int64)
     idx = g.choice(N, size=h, replace=False)
