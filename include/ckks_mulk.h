@@ -219,7 +219,11 @@ int ckks_plan_describe(const ckks_plan *plan, uint32_t *depth, uint32_t *rs_unit
  * 0 = Table II's rescale-unit count; 1 = limb (I)NTTs of the whole k-input
  * multiply at input `level` with K special primes and digits of `alpha`
  * primes (Algorithm 1 at inner nodes, relinearisation and relocated rescale
- * at the root). The cheapest tree's text (layered notation, NUL-terminated)
+ * at the root); 2 = precision: 10^6 x the largest degree of a tuple that an
+ * inner node rescales before relinearisation, plus criterion 1's count (the
+ * rounding error of a rescaled degree-t tuple decrypts multiplied by s^t,
+ * so the decoded product loses about log2 |s| bits per degree; not a
+ * criterion of the paper). The cheapest tree's text (layered notation, NUL-terminated)
  * is written to `text` (text_len bytes) and its cost to *cost; ties go to
  * fewer nodes, then the smaller text. The text is parsed back before it is
  * returned, so ckks_plan_create accepts it. ckks_plan_cost gives the same

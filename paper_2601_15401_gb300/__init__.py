@@ -290,7 +290,7 @@ class Context:
     def plan_cost(self, k: int, partition: str | None = None, criterion: str = "transforms",
                   level: int | None = None) -> float:
         v = ctypes.c_double()
-        crit = 0 if criterion == "rs_units" else 1
+        crit = {"rs_units": 0, "transforms": 1, "precision": 2}[criterion]
         _check(lib().ckks_plan_cost(self.plan(k, partition), crit, level if level is not None else self.L, self.K,
                                     self.alpha, ctypes.byref(v)), "ckks_plan_cost")
         return v.value
@@ -446,7 +446,7 @@ def plan_optimize(k: int, criterion: str = "rs_units", level: int = 0, K: int = 
     """(partition text, cost) of the cheapest valid tree; host only."""
     buf = ctypes.create_string_buffer(256)
     v = ctypes.c_double()
-    crit = 0 if criterion == "rs_units" else 1
+    crit = {"rs_units": 0, "transforms": 1, "precision": 2}[criterion]
     _check(lib().ckks_plan_optimize(k, crit, level, K, alpha, buf, 256, ctypes.byref(v)), "ckks_plan_optimize")
     return buf.value.decode(), v.value
 

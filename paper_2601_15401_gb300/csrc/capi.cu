@@ -174,7 +174,7 @@ int ckks_plan_describe(const ckks_plan *plan, uint32_t *depth, uint32_t *rs_unit
 
 int ckks_plan_optimize(uint32_t k, int criterion, uint32_t level, uint32_t K, uint32_t alpha, char *text,
                        size_t text_len, double *cost) {
-    if (!text || text_len == 0 || (criterion != 0 && criterion != 1) || (criterion == 1 && alpha == 0))
+    if (!text || text_len == 0 || criterion < 0 || criterion > 2 || (criterion >= 1 && alpha == 0))
         return CKKS_EINVAL;
     std::string best;
     double c = 0;
@@ -187,8 +187,8 @@ int ckks_plan_optimize(uint32_t k, int criterion, uint32_t level, uint32_t K, ui
 }
 
 int ckks_plan_cost(const ckks_plan *plan, int criterion, uint32_t level, uint32_t K, uint32_t alpha, double *cost) {
-    if (!plan || !cost || (criterion != 0 && criterion != 1) || (criterion == 1 && alpha == 0)) return CKKS_EINVAL;
-    if (criterion == 1 && (int)level <= plan->p.depth) return CKKS_ELEVEL;
+    if (!plan || !cost || criterion < 0 || criterion > 2 || (criterion >= 1 && alpha == 0)) return CKKS_EINVAL;
+    if (criterion >= 1 && (int)level <= plan->p.depth) return CKKS_ELEVEL;
     *cost = plan_cost(plan->p, criterion, (int)level, (int)K, (int)alpha);
     return CKKS_OK;
 }

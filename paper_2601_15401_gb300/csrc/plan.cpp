@@ -299,6 +299,14 @@ std::string layered_text(const TNode &root) {
 
 double plan_cost(const Plan &P, int criterion, int level, int K, int alpha) {
     if (criterion == kCostRsUnits) return P.rs_units;
+    if (criterion == kCostPrecision) {
+        // the largest degree (inputs below the node) of a tuple rescaled
+        // before relinearisation, then limb transforms as the tie-break
+        int deg = 0;
+        for (const PlanNode &n : P.nodes)
+            if (!n.root) deg = std::max(deg, n.size);
+        return 1e6 * deg + plan_cost(P, kCostTransforms, level, K, alpha);
+    }
     std::vector<int> lin, lout, polys;
     plan_levels(P, level, lin, lout, polys);
     double c = 0;
@@ -320,7 +328,7 @@ double plan_cost(const Plan &P, int criterion, int level, int K, int alpha) {
 int plan_optimize(int k, int criterion, int level, int K, int alpha, std::string &best_text, double &best_cost) {
     if (k < 2 || k > 12) return -1;
     const int D = ceil_log2(k);
-    if (criterion == kCostTransforms && level <= D) return -2;
+    if ((criterion == kCostTransforms || criterion == kCostPrecision) && level <= D) return -2;
     std::vector<TNode> roots;
     std::vector<std::vector<int>> all;
     std::vector<int> parts;

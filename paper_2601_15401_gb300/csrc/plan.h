@@ -26,7 +26,7 @@ int plan_build(Plan &P, int k, const char *partition);
 void plan_levels(const Plan &P, int level, std::vector<int> &lvl_in, std::vector<int> &lvl_out,
                  std::vector<int> &polys);
 
-enum { kCostRsUnits = 0, kCostTransforms = 1 };
+enum { kCostRsUnits = 0, kCostTransforms = 1, kCostPrecision = 2 };
 // cost of a plan: Table II rescale units, or limb (I)NTTs at an input level
 double plan_cost(const Plan &P, int criterion, int level, int K, int alpha);
 // cheapest valid partition of k inputs; 0 ok, -1 none, -2 level too low

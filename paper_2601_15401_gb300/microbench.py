@@ -36,6 +36,8 @@ def main():
     ap.add_argument("--partition", default=None, help="partition text for --op mul_k (default Table II)")
     ap.add_argument("--secret-h", type=int, default=0, help="--op precision: Hamming weight of s (0: uniform)")
     ap.add_argument("--scale-bits", type=int, default=50, help="--op precision: log2 of the encoding scale")
+    ap.add_argument("--criterion", default="table2", choices=["table2", "precision"],
+                    help="--op precision: Table II partitions or the precision search's")
     args = ap.parse_args()
     if args.op == "precision":
         return precision(args)
@@ -153,7 +155,10 @@ def precision(args):
     s, pk = keys[args.log_n]
     N, L, B, scale = ctx.N, ctx.L, args.batch, 2.0 ** args.scale_bits
     rows = {}
+    parts = {}
     for k in range(2, 13):
+        part = None if args.criterion == "table2" else G.plan_optimize(k, "precision", L, ctx.K, ctx.alpha)[0]
+        parts[k] = part or G.TABLE_II[k]
         zs = np.stack([synth.unit_disk_slots(synth.rng(11, k * 100 + i, stream=6), N // 2) for i in range(B * k)])
         ews = torch.empty(ctx.embed_workspace_size(B * k) // 8 + 1, dtype=torch.uint64, device="cuda")
         m = torch.empty((B * k, N), dtype=torch.int64, device="cuda")
@@ -169,11 +174,11 @@ def precision(args):
         ctx.encrypt_batch(m, v, e[0].contiguous(), e[1].contiguous(), pk, L, cts, ws)
         for t in cts:
             t.scale = scale
-        depth = ctx.plan_describe(k)["depth"]
+        depth = ctx.plan_describe(k, part)["depth"]
         out = torch.empty((B, 2, L - depth, N), dtype=torch.uint64, device="cuda")
         outs = [G.Tuple(out[b], 2, L - depth, L - depth) for b in range(B)]
-        mws = torch.empty(ctx.workspace_size(k, L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
-        ctx.mul_k_batch([cts[b * k:(b + 1) * k] for b in range(B)], evk, outs, mws)
+        mws = torch.empty(ctx.workspace_size(k, L, B, part) // 8 + 1, dtype=torch.uint64, device="cuda")
+        ctx.mul_k_batch([cts[b * k:(b + 1) * k] for b in range(B)], evk, outs, mws, partition=part)
         dec = torch.empty((B, N), dtype=torch.float64, device="cuda")
         dws = torch.empty(ctx.decrypt_batch_workspace_size(B) // 8 + 1, dtype=torch.uint64, device="cuda")
         ctx.decrypt_batch(outs, s, dec, dws)
@@ -181,11 +186,12 @@ def precision(args):
         ctx.decode(dec, outs[0].scale, zo, ews)
         want = np.prod(zs.reshape(B, k, N // 2), axis=1)
         err = float(np.abs(zo.cpu().numpy() - want).max())
-        rows[k] = {"max_abs_err": err, "log2": round(float(np.log2(err)), 1) if err > 0 else None}
+        rows[k] = {"max_abs_err": err, "log2": round(float(np.log2(err)), 1) if err > 0 else None,
+                   "partition": parts[k]}
         del ct, ws, mws, out, dec, ews, m
         torch.cuda.empty_cache()
     print(json.dumps({"op": "precision", "log_n": args.log_n, "L": L, "K": ctx.K, "dnum": ctx.dnum,
-                      "scale_bits": args.scale_bits, "batch": B,
+                      "scale_bits": args.scale_bits, "batch": B, "criterion": args.criterion,
                       "secret": f"Hamming weight {h}" if h else "uniform ternary", "per_k": rows}))
 
 

@@ -109,3 +109,34 @@ def test_transform_search_beats_or_ties_every_table_ii_tree(L):
         lib().ckks_plan_destroy(h)
         assert best <= c.value
         assert oplan.valid(oplan.parse(best_text, k), k)
+
+
+def test_precision_criterion_minimises_inner_degree():
+    """Criterion "precision": the chosen tree keeps the depth rule (the
+    oracle's parser and checker), its cost carries the largest degree of a
+    tuple rescaled below the root, that degree is never above Table II's,
+    and it is strictly below it for k = 6 and k = 12."""
+    import paper_2601_15401_gb300 as G
+    from oracle import plan as P
+
+    def inner_degree(text, k):
+        worst = [0]
+
+        def go(n, root):
+            if n.is_leaf:
+                return 1
+            d = sum(go(c, False) for c in n.children)
+            if not root:
+                worst[0] = max(worst[0], d)
+            return d
+        go(P.parse(text, k), True)
+        return worst[0]
+
+    for k in range(2, 13):
+        text, cost = G.plan_optimize(k, "precision", 24, 8, 8)
+        assert P.valid(P.parse(text, k), k)
+        d = inner_degree(text, k)
+        assert int(cost // 1e6) == d
+        assert d <= inner_degree(P.TABLE_II[k], k)
+    assert inner_degree(G.plan_optimize(12, "precision", 24, 8, 8)[0], 12) == 4
+    assert inner_degree(G.plan_optimize(6, "precision", 24, 8, 8)[0], 6) == 2
