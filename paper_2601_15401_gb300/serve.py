@@ -410,7 +410,7 @@ def latency_stats(reqs: list[Request]) -> dict:
 # the mixed workload (k uniform in 2..12, N in {2^14, 2^15, 2^16},
 # level uniform in [k, 24]) served at a Poisson rate
 # ---------------------------------------------------------------------------
-def mixed_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size=64, k_range=(2, 12)):
+def mixed_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size=64, k_range=(2, 12), partitions=None):
     import numpy as np
     g = np.random.default_rng(seed)
     arr = poisson_arrivals(rate, seconds, g)
@@ -420,11 +420,12 @@ def mixed_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size=64,
         log_n = int(g.choice(log_ns))
         level = int(g.integers(k, L + 1))
         cts = tuple(int(x) for x in g.integers(0, pool_size, size=k))
-        reqs.append(Request(i, log_n, k, level, cts, arrival=t))
+        reqs.append(Request(i, log_n, k, level, cts, arrival=t, partition=(partitions or {}).get(k)))
     return reqs
 
 
-def plaintext_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size=16, k_range=(2, 12)):
+def plaintext_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size=16, k_range=(2, 12),
+                       partitions=None):
     """The mixed workload with slot vectors instead of pool ciphertexts: each
     request multiplies k slot vectors taken from a per-N pool of unit-disk
     vectors; its encryption noise is seeded by the request."""
@@ -440,7 +441,7 @@ def plaintext_requests(rate, seconds, seed, log_ns=(14, 15, 16), L=24, pool_size
         log_n = int(g.choice(log_ns))
         level = int(g.integers(k, L + 1))
         idx = [int(x) for x in g.integers(0, pool_size, size=k)]
-        reqs.append(Request(i, log_n, k, level, tuple(idx), arrival=t,
+        reqs.append(Request(i, log_n, k, level, tuple(idx), arrival=t, partition=(partitions or {}).get(k),
                             slots=np.stack([pools[log_n][j] for j in idx]), seed=seed * 1000003 + i))
     return reqs
 
@@ -489,7 +490,13 @@ def main():
     ap.add_argument("--plaintext", action="store_true",
                     help="requests carry slot vectors: encode, encrypt, multiply, decrypt, decode on the device")
     ap.add_argument("--k-max", type=int, default=12)
+    ap.add_argument("--criterion", default="table2", choices=["table2", "precision"],
+                    help="partitions: Table II, or the precision search's (smallest inner tuple degree)")
     args = ap.parse_args()
+    parts = None
+    if args.criterion == "precision":
+        from . import plan_optimize
+        parts = {k: plan_optimize(k, "precision", 24, 8, 8)[0] for k in range(2, args.k_max + 1)}
     log_ns = tuple(int(x) for x in args.log_ns.split(","))
     h = args.secret_h or None
     contexts, pools = build_gpu_state(log_ns, pool_size=1 if args.plaintext else 64, secret_h=h)
@@ -498,12 +505,12 @@ def main():
                               ws_bytes=int(args.ws_gb * (1 << 30)), keep_results=True)
 
         def make(rate, seconds, seed, lns):
-            return plaintext_requests(rate, seconds, seed, lns, k_range=(2, args.k_max))
+            return plaintext_requests(rate, seconds, seed, lns, k_range=(2, args.k_max), partitions=parts)
     else:
         be = GpuBackend(contexts, pools, n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)))
 
         def make(rate, seconds, seed, lns):
-            return mixed_requests(rate, seconds, seed, lns, k_range=(2, args.k_max))
+            return mixed_requests(rate, seconds, seed, lns, k_range=(2, args.k_max), partitions=parts)
     # the cap covers everything on the device: keys, pools, tables and stream
     # workspaces are resident; batches are admitted within what is left
     resident = be.resident_bytes()
@@ -524,7 +531,7 @@ def main():
             e = float(np.abs(be.results[r.rid] - np.prod(r.slots, axis=0)).max())
             err[r.k] = max(err.get(r.k, 0.0), e)
         extra = {"mode": "plaintext in / plaintext out", "max_abs_slot_error_per_k": dict(sorted(err.items())),
-                 "secret": f"Hamming weight {h}" if h else "uniform ternary"}
+                 "secret": f"Hamming weight {h}" if h else "uniform ternary", "partitions": args.criterion}
     print(json.dumps({"metric": "served k-input ct-mults/s (Poisson arrivals, mixed k, N, level)",
                       "offered_rate": args.rate, "seconds": args.seconds, "requests": len(reqs),
                       "completed": len(sched.completed), "wall_s": round(wall, 3),
