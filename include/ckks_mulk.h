@@ -252,8 +252,10 @@ int ckks_mul_k(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, const ckks_e
 /* ckks_mul_k_batch: `batch` independent products with one plan and one key
  * set, each kernel launch covering the whole batch. ct is [batch][k] tuples,
  * out is [batch]. For every input position u, ct[b*k+u].data must be
- * ct[u].data + b * stride_u for one stride_u (likewise for out); the same
- * level, poly_stride and n_polys for all b. */
+ * ct[u].data + b * stride_u for one stride_u (likewise for out, whose
+ * stride must not be 0: two batch elements cannot share one output, which
+ * is CKKS_EINVAL; inputs may repeat); the same level, poly_stride and
+ * n_polys for all b. The batched calls below follow the same rule. */
 int ckks_mul_k_batch(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uint32_t batch, const ckks_evk_set *evk,
                      const ckks_plan *plan, ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream);
 

@@ -245,6 +245,7 @@ static int mul_k_common(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uin
         if (out[b].poly_stride < out_level || out[b].poly_stride != out[0].poly_stride) return CKKS_EINVAL;
     }
     i64 obs = batch > 1 ? (i64)(out[1].data - out[0].data) : 0;
+    if (batch > 1 && obs == 0) return CKKS_EINVAL;  // batch elements would write one output
     for (uint32_t b = 0; b < batch; ++b)
         if (out[b].data != out[0].data + b * obs) return CKKS_EINVAL;
     size_t need = mul_k_ws_bytes(C, P, (int)level, (int)batch);
@@ -310,7 +311,7 @@ int ckks_mul2_batch(ckks_context *ctx, const ckks_tuple *a, const ckks_tuple *b,
         if ((int)out[i].poly_stride < level - 1 || out[i].poly_stride != out[0].poly_stride) return CKKS_EINVAL;
     }
     i64 as = batch_stride(a, batch), bs = batch_stride(b, batch), os = batch_stride(out, batch);
-    if (as < 0 || bs < 0 || os < 0) return CKKS_EINVAL;
+    if (as < 0 || bs < 0 || os < 0 || (batch > 1 && os == 0)) return CKKS_EINVAL;
     size_t need = mul2_ws_bytes(C, level, (int)batch);
     if (!workspace || ws_bytes < need) return CKKS_ENOMEM;
     cudaSetDevice(C.device);
@@ -496,7 +497,7 @@ int ckks_rotate_batch(ckks_context *ctx, const ckks_tuple *in, uint32_t batch, u
         if ((int)out[i].poly_stride < level || out[i].poly_stride != out[0].poly_stride) return CKKS_EINVAL;
     }
     i64 is = batch_stride(in, batch), os = batch_stride(out, batch);
-    if (is < 0 || os < 0) return CKKS_EINVAL;
+    if (is < 0 || os < 0 || (batch > 1 && os == 0)) return CKKS_EINVAL;
     size_t need = rotate_ws_bytes(C, level, (int)batch);
     if (!workspace || ws_bytes < need) return CKKS_ENOMEM;
     cudaSetDevice(C.device);

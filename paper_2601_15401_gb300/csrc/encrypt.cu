@@ -204,7 +204,7 @@ int ckks_encrypt_batch(ckks_context *ctx, const int64_t *m, const int64_t *v, co
         if (out[b].poly_stride < level || out[b].poly_stride != out[0].poly_stride) return CKKS_EINVAL;
     }
     const i64 os = spacing(out, batch);
-    if (os < 0) return CKKS_EINVAL;
+    if (os < 0 || (batch > 1 && os == 0)) return CKKS_EINVAL;
     if (ws_bytes < enc_batch_ws(C, level, batch)) return CKKS_ENOMEM;
     cudaSetDevice(C.device);
     cudaStream_t st = (cudaStream_t)stream;
