@@ -56,6 +56,7 @@ extern "C" {
 #define CKKS_ECUDA (-5)    /* CUDA error (launch or sticky) */
 #define CKKS_ETIMEOUT (-6) /* a bounded device wait ran out */
 #define CKKS_EBUSY (-7)    /* admission refused */
+#define CKKS_ECHECK (-8)   /* integrity check failed: a residue >= q, or resident keys changed */
 
 typedef struct ckks_context ckks_context;
 typedef struct ckks_evk_set ckks_evk_set;
@@ -115,6 +116,14 @@ int ckks_keygen_evk(ckks_context *ctx, uint32_t t_max, const int64_t *s, const u
  * borrowed until ckks_evk_set_destroy; do not read it as plain keys after. */
 int ckks_evk_set_create(ckks_context *ctx, uint32_t t_max, uint64_t *keys, void *stream, ckks_evk_set **out);
 void ckks_evk_set_destroy(ckks_evk_set *set);
+
+/* Integrity checks (failure detection; the paper has no counterpart).
+ * ckks_evk_set_create also takes a position-dependent 64-bit checksum of
+ * the prepared keys (it synchronises `stream` once for that);
+ * ckks_evk_verify recomputes it and returns CKKS_ECHECK if the resident
+ * keys changed since (a stray write into the borrowed buffer), CKKS_OK if
+ * not. Synchronous on `stream`. */
+int ckks_evk_verify(ckks_evk_set *set, void *stream);
 
 /* ------------------------------------------------------ around the product
  * Section II's public key, encryption and decryption, on the device.
@@ -357,13 +366,23 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
  * replaces; its residues differ from the combined form's by the same small
  * integer W in [0, K (n - 2)] in every limb, the extra wraps of Eq. 5's
  * P-residues; it needs no more workspace). CKKS_EINVAL for an unknown key
- * or a value out of range. */
+ * or a value out of range.
+ * Debugging aids: "check_residues" 1 = ckks_mul_k / ckks_mul_k_batch count
+ * residues outside [0, q) in their inputs and after every stage (tensor
+ * product, Algorithm 1 rescale, relinearisation, root rescale), then
+ * synchronise the stream and return CKKS_ECHECK if any were found (results
+ * are still written); "nvtx" 1 = NVTX ranges around each stage's launches,
+ * for profilers that filter by range. Both default to 0. */
 int ckks_tune_set(ckks_context *ctx, const char *key, int value);
 int ckks_tune_get(const ckks_context *ctx, const char *key, int *value);
 
 /* ckks_check: CKKS_ECUDA if a CUDA error is pending on the context's device
  * (sticky launch error or cudaGetLastError), else CKKS_OK. */
 int ckks_check(ckks_context *ctx);
+/* ckks_check_residues: *bad = number of residues outside [0, q_j) in the
+ * tuple's active limbs (limb j checked against q_j). Synchronous on
+ * `stream`; a valid tuple gives 0. */
+int ckks_check_residues(ckks_context *ctx, const ckks_tuple *t, uint64_t *bad, void *stream);
 const char *ckks_strerror(int code);
 
 #ifdef __cplusplus

@@ -145,6 +145,14 @@ class Context:
         _check(lib().ckks_encrypt_workspace_size(self._h, ctypes.byref(n)), "ckks_encrypt_workspace_size")
         return n.value
 
+    def check_residues(self, t: "Tuple", stream=None) -> int:
+        """Number of residues outside [0, q) in the tuple's active limbs."""
+        c = t.c()
+        n = ctypes.c_uint64()
+        _check(lib().ckks_check_residues(self._h, ctypes.byref(c), ctypes.byref(n), _stream(stream)),
+               "ckks_check_residues")
+        return n.value
+
     def embed_workspace_size(self, batch: int = 1) -> int:
         n = ctypes.c_size_t()
         _check(lib().ckks_embed_workspace_size(self._h, batch, ctypes.byref(n)), "ckks_embed_workspace_size")
@@ -454,6 +462,14 @@ def plan_optimize(k: int, criterion: str = "rs_units", level: int = 0, K: int = 
 class EvkSet:
     def __init__(self, ctx: Context, h, keys, t_max: int):
         self.ctx, self._h, self.keys, self.t_max = ctx, h, keys, t_max
+
+    def verify(self, stream=None) -> bool:
+        """True if the resident keys still match the checksum taken at creation."""
+        rc = lib().ckks_evk_verify(self._h, _stream(stream))
+        if rc == -8:
+            return False
+        _check(rc, "ckks_evk_verify")
+        return True
 
     def close(self):
         if self._h:

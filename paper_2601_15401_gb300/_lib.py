@@ -8,7 +8,7 @@ from functools import lru_cache
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 ERRORS = {0: "CKKS_OK", -1: "CKKS_EINVAL", -2: "CKKS_ELEVEL", -3: "CKKS_EKEY", -4: "CKKS_ENOMEM",
-          -5: "CKKS_ECUDA", -6: "CKKS_ETIMEOUT", -7: "CKKS_EBUSY"}
+          -5: "CKKS_ECUDA", -6: "CKKS_ETIMEOUT", -7: "CKKS_EBUSY", -8: "CKKS_ECHECK"}
 
 
 class CkksError(RuntimeError):
@@ -37,6 +37,8 @@ SIGNATURES = {
     "ckks_rotate_workspace_size": [V, U32, U32, V],
     "ckks_rotate": [V, V, U32, V, V, V, SZ, V],
     "ckks_rotate_batch": [V, V, U32, U32, V, V, V, SZ, V],
+    "ckks_evk_verify": [V, V],
+    "ckks_check_residues": [V, V, V, V],
     "ckks_encrypt_workspace_size": [V, V],
     "ckks_encrypt_batch_workspace_size": [V, U32, U32, V],
     "ckks_encrypt_batch": [V, V, V, V, V, U32, V, U32, V, V, SZ, V],

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.environ.get("CKKS_MULK_LIB", os.path.join(HERE, "libckks_mulk.so"))
-SOURCES = ["ntt.cu", "rns.cu", "context.cu", "engine.cu", "capi.cu", "plan.cpp", "noalloc.cu", "encrypt.cu", "galois.cu", "embed.cu"]
+SOURCES = ["ntt.cu", "rns.cu", "context.cu", "engine.cu", "capi.cu", "plan.cpp", "noalloc.cu", "encrypt.cu", "galois.cu", "embed.cu", "check.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -53,7 +53,7 @@ def build(force: bool = False, extra: list[str] | None = None, verbose: bool = F
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

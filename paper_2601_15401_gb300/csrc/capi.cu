@@ -19,7 +19,30 @@ struct ckks_evk_set {
     ckks_context *ctx;
     u64 *keys;
     uint32_t t_max;
+    unsigned long long sum;  // checksum of the prepared keys, taken at creation
 };
+
+static long long evk_words(const Context &C, uint32_t t_max) {
+    return (long long)(t_max - 1) * C.dnum * 2 * (C.L + C.K) * C.N;
+}
+
+// checksum of the set's key buffer (synchronous on `st`)
+static cudaError_t evk_checksum(const Context &C, const u64 *keys, uint32_t t_max, cudaStream_t st,
+                                unsigned long long &sum) {
+    cudaError_t e = cudaMemsetAsync(C.d_check + 1, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_checksum(C, keys, evk_words(C, t_max), C.d_check + 1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sum, C.d_check + 1, sizeof(sum), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+// reads and clears the residue-check counter (synchronous on `st`)
+static cudaError_t take_residue_count(const Context &C, cudaStream_t st, unsigned long long &bad) {
+    cudaError_t e = cudaMemcpyAsync(&bad, C.d_check, sizeof(bad), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(C.d_check, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
 struct ckks_plan {
     Plan p;
 };
@@ -140,13 +163,40 @@ int ckks_evk_set_create(ckks_context *ctx, uint32_t t_max, uint64_t *keys, void 
     long long rows = (long long)(t_max - 1) * C.dnum * 2 * (C.L + C.K);
     cudaError_t err = launch_keyprep(C, (u64 *)keys, rows, S(stream));
     if (err != cudaSuccess) return cuda_fail(ctx, err);
-    ckks_evk_set *set = new (std::nothrow) ckks_evk_set{ctx, (u64 *)keys, t_max};
+    unsigned long long sum = 0;
+    err = evk_checksum(C, (const u64 *)keys, t_max, S(stream), sum);
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    ckks_evk_set *set = new (std::nothrow) ckks_evk_set{ctx, (u64 *)keys, t_max, sum};
     if (!set) return CKKS_ENOMEM;
     *out = set;
     return CKKS_OK;
 }
 
 void ckks_evk_set_destroy(ckks_evk_set *set) { delete set; }
+
+int ckks_evk_verify(ckks_evk_set *set, void *stream) {
+    if (!set || !set->ctx) return CKKS_EINVAL;
+    const Context &C = set->ctx->c;
+    cudaSetDevice(C.device);
+    unsigned long long sum = 0;
+    cudaError_t err = evk_checksum(C, set->keys, set->t_max, S(stream), sum);
+    if (err != cudaSuccess) return cuda_fail(set->ctx, err);
+    return sum == set->sum ? CKKS_OK : CKKS_ECHECK;
+}
+
+int ckks_check_residues(ckks_context *ctx, const ckks_tuple *t, uint64_t *bad, void *stream) {
+    if (!ctx || !t || !bad || !tuple_ok(t, ctx->c.L)) return CKKS_EINVAL;
+    const Context &C = ctx->c;
+    cudaSetDevice(C.device);
+    cudaStream_t st = S(stream);
+    unsigned long long n = 0;
+    cudaError_t err = cudaMemsetAsync(C.d_check, 0, sizeof(unsigned long long), st);
+    if (err == cudaSuccess) err = launch_range_check(C, tview(*t, C.N), 1, (int)t->n_polys, (int)t->level, st);
+    if (err == cudaSuccess) err = take_residue_count(C, st, n);
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    *bad = n;
+    return CKKS_OK;
+}
 
 int ckks_plan_create(ckks_context *ctx, uint32_t k, const char *partition, ckks_plan **out) {
     (void)ctx;
@@ -256,6 +306,12 @@ static int mul_k_common(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uin
                           (int)evk->t_max, ws, ws_bytes, S(stream), err);
     if (rc == -3) return CKKS_EKEY;
     if (err != cudaSuccess || rc != 0) return cuda_fail(ctx, err == cudaSuccess ? cudaErrorUnknown : err);
+    if (C.tune_check_residues) {
+        unsigned long long bad = 0;
+        err = take_residue_count(C, S(stream), bad);
+        if (err != cudaSuccess) return cuda_fail(ctx, err);
+        if (bad) return CKKS_ECHECK;
+    }
     for (uint32_t b = 0; b < batch; ++b) {
         std::vector<double> sc(k);
         for (uint32_t u = 0; u < k; ++u) sc[u] = ct[b * k + u].scale;
@@ -645,6 +701,8 @@ static int *tune_slot(ckks_context *ctx, const char *key, int &lo, int &hi) {
     if (!strcmp(key, "inner_rescale")) { lo = 0; hi = 2; return &ctx->c.tune_inner_rescale; }
     if (!strcmp(key, "root_rescale")) { lo = 0; hi = 1; return &ctx->c.tune_root_rescale; }
     if (!strcmp(key, "moddown")) { lo = 0; hi = 1; return &ctx->c.tune_moddown; }
+    if (!strcmp(key, "check_residues")) { lo = 0; hi = 1; return &ctx->c.tune_check_residues; }
+    if (!strcmp(key, "nvtx")) { lo = 0; hi = 1; return &ctx->c.tune_nvtx; }
     return nullptr;
 }
 
@@ -688,6 +746,7 @@ const char *ckks_strerror(int code) {
     case CKKS_ECUDA: return "CUDA error";
     case CKKS_ETIMEOUT: return "device wait timed out";
     case CKKS_EBUSY: return "admission refused";
+    case CKKS_ECHECK: return "integrity check failed (a residue >= q, or the resident keys changed)";
     default: return "unknown error";
     }
 }

@@ -241,6 +241,7 @@ int context_build(Context &C, const uint32_t log_n, const uint32_t L, const uint
         size_t bytes;
         void **dst;
     };
+    static const unsigned long long zero_words[2] = {0, 0};  // integrity-check counter
     std::vector<Piece> pieces = {
         {mods.data(), mods.size() * sizeof(ModQ), (void **)&C.d_mods},
         {twf.data(), twf.size() * sizeof(ulonglong2), (void **)&C.d_tw_fwd},
@@ -257,6 +258,7 @@ int context_build(Context &C, const uint32_t log_n, const uint32_t L, const uint
         {bcon.data(), bcon.size() * sizeof(u64), (void **)&C.d_bconv_c},
         {gt.data(), gt.size() * sizeof(Shoup), (void **)&C.d_g},
         {pgadget.data(), pgadget.size() * sizeof(Shoup), (void **)&C.d_pgadget},
+        {zero_words, sizeof(zero_words), (void **)&C.d_check},
     };
     size_t total = 0;
     for (auto &pc : pieces) total += (pc.bytes + 255) / 256 * 256;

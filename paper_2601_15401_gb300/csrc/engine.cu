@@ -20,6 +20,7 @@
 //   relocated rescale (Section IV): the rescale chain among the mu top limbs
 //   of c*, then one NTT per surviving limb with the Eq. 17 combination
 //   (with the self term) fused into its load -> output, NTT domain.
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <cmath>
 
@@ -428,6 +429,26 @@ static cudaError_t root_rescale(const Context &C, int B, int level, int mu, Limb
 // ---------------------------------------------------------------------------
 // k-input multiply over a plan
 // ---------------------------------------------------------------------------
+// NVTX range around the enqueueing of one stage (tunable "nvtx")
+struct NvtxRange {
+    bool on;
+    NvtxRange(const Context &C, const char *name) : on(C.tune_nvtx != 0) {
+        if (on) nvtxRangePushA(name);
+    }
+    ~NvtxRange() {
+        if (on) nvtxRangePop();
+    }
+};
+
+// tunable "check_residues": count residues >= q of a stage's output
+#define CHECK_STAGE(v, polys, lvl)                                                        \
+    do {                                                                                  \
+        if (C.tune_check_residues && !ws.dry) {                                          \
+            err = launch_range_check(C, (v), B, (polys), (lvl), st);                      \
+            if (err != cudaSuccess) return -5;                                            \
+        }                                                                                 \
+    } while (0)
+
 int run_mul_k(const Context &C, const Plan &P, int level, int B, const LimbView *in, LimbView out, const u64 *keys,
               int t_max, Ws &ws, cudaStream_t st, cudaError_t &err) {
     std::vector<int> lin, lout, polys;
@@ -435,6 +456,7 @@ int run_mul_k(const Context &C, const Plan &P, int level, int B, const LimbView 
     const int N = C.N;
     std::vector<LimbView> node_out(P.nodes.size());
     err = cudaSuccess;
+    for (int u = 0; u < P.k; ++u) CHECK_STAGE(in[u], 2, level);
     for (size_t i = 0; i < P.nodes.size(); ++i) {
         const PlanNode &nd = P.nodes[i];
         const int lv = lin[i];
@@ -456,13 +478,17 @@ int run_mul_k(const Context &C, const Plan &P, int level, int B, const LimbView 
         LimbView dv = view(d, (i64)np * lv * N, (i64)lv * N);
         T.out = dv;
         if (!ws.dry) {
+            NvtxRange r(C, nd.root ? "root: tensor product" : "node: tensor product");
             err = launch_tensor(C, T, st);
             if (err != cudaSuccess) return -5;
         }
+        CHECK_STAGE(dv, np, lv);
         if (!nd.root) {
+            NvtxRange r(C, "node: multi-level rescale (Algorithm 1)");
             err = multi_rs(C, ws, B, np, lv, nd.mu, dv, dv, st);
             if (err != cudaSuccess) return -5;
             node_out[i] = dv;  // level lv - mu, poly stride lv
+            CHECK_STAGE(dv, np, lv - nd.mu);
         } else {
             const int n = np - 1;
             if (n > t_max) return -3;
@@ -480,13 +506,19 @@ int run_mul_k(const Context &C, const Plan &P, int level, int B, const LimbView 
                     if (err != cudaSuccess) return -5;
                 }
             } else {
-                err = relin_core(C, ws, B, n, lv, dv, keys, t_max, false, cv, st);
-                if (err != cudaSuccess) return -5;
+                {
+                    NvtxRange r(C, "root: relinearisation (ModUp, key MAC, ModDown)");
+                    err = relin_core(C, ws, B, n, lv, dv, keys, t_max, false, cv, st);
+                    if (err != cudaSuccess) return -5;
+                }
+                CHECK_STAGE(cv, 2, lv);
                 if (!ws.dry) {
+                    NvtxRange r(C, "root: relocated rescale");
                     err = root_rescale(C, B, lv, nd.mu, cv, out, st);
                     if (err != cudaSuccess) return -5;
                 }
             }
+            CHECK_STAGE(out, 2, lv - nd.mu);
         }
     }
     return 0;

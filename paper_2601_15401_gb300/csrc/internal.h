@@ -113,6 +113,7 @@ struct Context {
     u64 *d_bconv_c = nullptr;         // [L+1][dnum][alpha][L+K] Montgomery [(Q_beta/q_j) mod x] R
     Shoup *d_g = nullptr;             // Eq. 16 tables, offsets g_off[level][mu]
     std::vector<std::vector<size_t>> g_off;
+    unsigned long long *d_check = nullptr;  // [2] residue-check counter (zero between calls)
     Shoup *d_pgadget = nullptr;       // [dnum][L+K] P G_beta mod x (Q limbs), 0 for P limbs
     void *d_block = nullptr;          // one allocation holding all tables
     std::atomic<unsigned long long> counters[OP_COUNT];
@@ -129,6 +130,11 @@ struct Context {
     // key switching: 0 = one ModDown over the summed keys (Eq. 15), 1 = one
     // ModDown per key, summed afterwards (the form before Eq. 15)
     int tune_moddown = 0;
+    // debugging aids: 1 = count residues >= q in the inputs and after every
+    // stage of a k-input product (the call then synchronises and fails with
+    // CKKS_ECHECK on a violation); 1 = NVTX ranges per tree node and stage
+    int tune_check_residues = 0;
+    int tune_nvtx = 0;
 };
 
 // Records CUDA events around one launch on its stream when the hook is on;

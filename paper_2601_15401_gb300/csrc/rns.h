@@ -59,6 +59,10 @@ cudaError_t launch_signed_to_res(const Context &C, const long long *v, u64 *out,
 cudaError_t launch_pointwise_mul(const Context &C, u64 *St, const u64 *S, cudaStream_t st);
 cudaError_t launch_automorphism(const Context &C, LimbView in, LimbView out, const AutoMap &map, int batch,
                                 int level, uint32_t g, cudaStream_t st);
+// integrity checks (check.cu): residues >= q are counted into C.d_check[0];
+// the checksum of n words is added to *out (device)
+cudaError_t launch_range_check(const Context &C, LimbView v, int batch, int polys, int level, cudaStream_t st);
+cudaError_t launch_checksum(const Context &C, const u64 *w, long long n, unsigned long long *out, cudaStream_t st);
 cudaError_t launch_add_limbs(const Context &C, LimbView dst, LimbView src, int batch, int polys, int level,
                              cudaStream_t st);
 cudaError_t launch_keygen(const Context &C, const u64 *S, const u64 *St, const u64 *E, const u64 *a, u64 *ek,
