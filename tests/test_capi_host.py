@@ -38,6 +38,14 @@ def test_every_declared_symbol_is_exported(L):
 def test_strerror(L):
     assert L.ckks_strerror(0) == b"ok"
     assert L.ckks_strerror(-4) == b"workspace too small"
+    assert b"integrity" in L.ckks_strerror(-8)
+    # every code the header defines has its own message
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "ckks_mulk.h")).read()
+    codes = [int(v) for v in re.findall(r"#define CKKS_E\w+ \((-\d+)\)", hdr)]
+    assert len(codes) >= 8
+    for c in codes:
+        assert L.ckks_strerror(c) != b"unknown error", c
 
 
 def _describe(L, k, part):
