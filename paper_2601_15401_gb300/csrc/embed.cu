@@ -47,11 +47,18 @@ __device__ __forceinline__ uint32_t pow5(uint32_t j, uint32_t two_n) {
     return (uint32_t)x;
 }
 
+// T[j] = exp(i pi j / N), j < 2N (one table per call, in the workspace):
+// exp(sign 2 pi i x / N) = T[2x] or its conjugate
+__device__ __forceinline__ double2 root(const double2 *T, long long two_x, int sign) {
+    const double2 w = T[two_x];
+    return sign > 0 ? w : make_double2(w.x, -w.y);
+}
+
 // kTC radix-2 transforms of length 2^lg held in s[t * len + ...] in
 // bit-reversed order; natural order on return. sign = +1 or -1.
-__device__ void smem_fft(double2 *s, int lg, int sign, double2 *tw) {
+__device__ void smem_fft(double2 *s, int lg, int sign, double2 *tw, const double2 *T, int log_n) {
     const int len = 1 << lg;
-    for (int j = threadIdx.x; j < len / 2; j += blockDim.x) tw[j] = cis_pi(sign * 2.0 * j / len);
+    for (int j = threadIdx.x; j < len / 2; j += blockDim.x) tw[j] = root(T, (2ll * j) << (log_n - lg), sign);
     __syncthreads();
     for (int h = 1; h < len; h <<= 1) {
         const int stride = len / (2 * h);
@@ -70,7 +77,8 @@ __device__ void smem_fft(double2 *s, int lg, int sign, double2 *tw) {
 
 // Step 1 (columns): for columns n2 = c0..c0+kTC-1,
 // Y[k1][n2] = exp(sign 2 pi i n2 k1 / N) sum_n1 x[N2 n1 + n2] exp(sign 2 pi i n1 k1 / N1)
-__global__ void __launch_bounds__(kThr) fft_cols_kernel(const double2 *x, double2 *y, int lg1, int lg2, int sign) {
+__global__ void __launch_bounds__(kThr) fft_cols_kernel(const double2 *x, double2 *y, int lg1, int lg2, int sign,
+                                                        const double2 *T) {
     extern __shared__ double2 sm[];
     const int N1 = 1 << lg1, N2 = 1 << lg2, N = N1 * N2;
     const int tc = N2 < kTC ? N2 : kTC;
@@ -83,17 +91,18 @@ __global__ void __launch_bounds__(kThr) fft_cols_kernel(const double2 *x, double
     }
     for (int u = threadIdx.x + tc * N1; u < kTC * N1; u += blockDim.x) s[u] = make_double2(0, 0);
     __syncthreads();
-    smem_fft(s, lg1, sign, tw);
+    smem_fft(s, lg1, sign, tw, T, lg1 + lg2);
     for (int u = threadIdx.x; u < tc * N1; u += blockDim.x) {
         const int k1 = u / tc, c = u % tc;
         const int n2 = c0 + c;
         const long long e = ((long long)n2 * k1) % N;  // exact argument reduction
-        y[off + (size_t)k1 * N2 + n2] = cmul(s[c * N1 + k1], cis_pi(sign * 2.0 * (double)e / N));
+        y[off + (size_t)k1 * N2 + n2] = cmul(s[c * N1 + k1], root(T, 2 * e, sign));
     }
 }
 
 // Step 2 (rows): X[k1 + N1 k2] = sum_n2 Y[k1][n2] exp(sign 2 pi i n2 k2 / N2)
-__global__ void __launch_bounds__(kThr) fft_rows_kernel(const double2 *y, double2 *X, int lg1, int lg2, int sign) {
+__global__ void __launch_bounds__(kThr) fft_rows_kernel(const double2 *y, double2 *X, int lg1, int lg2, int sign,
+                                                        const double2 *T) {
     extern __shared__ double2 sm[];
     const int N1 = 1 << lg1, N2 = 1 << lg2, N = N1 * N2;
     const int tr = N1 < kTC ? N1 : kTC;
@@ -106,7 +115,7 @@ __global__ void __launch_bounds__(kThr) fft_rows_kernel(const double2 *y, double
     }
     for (int u = threadIdx.x + tr * N2; u < kTC * N2; u += blockDim.x) s[u] = make_double2(0, 0);
     __syncthreads();
-    smem_fft(s, lg2, sign, tw);
+    smem_fft(s, lg2, sign, tw, T, lg1 + lg2);
     for (int u = threadIdx.x; u < tr * N2; u += blockDim.x) {
         const int k2 = u / tr, r = u % tr;
         X[off + (size_t)(r0 + r) + (size_t)N1 * k2] = s[r * N2 + k2];
@@ -114,11 +123,11 @@ __global__ void __launch_bounds__(kThr) fft_rows_kernel(const double2 *y, double
 }
 
 // decode, before the DFT: x_i = m_i omega^i
-__global__ void twist_kernel(const double *m, double2 *x, int N) {
+__global__ void twist_kernel(const double *m, double2 *x, int N, const double2 *T) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const size_t o = (size_t)blockIdx.y * N + i;
-    const double2 w = cis_pi((double)i / N);
+    const double2 w = T[i];
     x[o] = make_double2(m[o] * w.x, m[o] * w.y);
 }
 
@@ -145,13 +154,19 @@ __global__ void scatter_kernel(const double *z, double2 *V, int N, double scale)
 }
 
 // encode, after: m_i = round(Re(omega^-i w_i) / N)
-__global__ void untwist_round_kernel(const double2 *w, long long *m, int N) {
+__global__ void untwist_round_kernel(const double2 *w, long long *m, int N, const double2 *T) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const size_t o = (size_t)blockIdx.y * N + i;
-    const double2 c = cis_pi(-(double)i / N);
+    const double2 c = make_double2(T[i].x, -T[i].y);
     const double re = w[o].x * c.x - w[o].y * c.y;
     m[o] = llrint(re / N);
+}
+
+// T[j] = exp(i pi j / N) for j < 2N
+__global__ void roots_kernel(double2 *T, int N) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < 2 * N) T[j] = cis_pi((double)j / N);
 }
 
 int geometry(int log_n, int &lg1, int &lg2) {
@@ -161,7 +176,7 @@ int geometry(int log_n, int &lg1, int &lg2) {
 }
 
 cudaError_t dft(const Context &C, const double2 *in, double2 *tmp, double2 *out, int batch, int sign,
-                cudaStream_t st) {
+                const double2 *T, cudaStream_t st) {
     int lg1, lg2;
     geometry(C.log_n, lg1, lg2);
     const int N1 = 1 << lg1, N2 = 1 << lg2;
@@ -169,15 +184,22 @@ cudaError_t dft(const Context &C, const double2 *in, double2 *tmp, double2 *out,
     const size_t sm2 = (size_t)(kTC * N2 + N2 / 2 + 1) * sizeof(double2);
     const int tc = N2 < kTC ? N2 : kTC, tr = N1 < kTC ? N1 : kTC;
     count_kernel(C);
-    fft_cols_kernel<<<dim3(N2 / tc, batch), kThr, sm1, st>>>(in, tmp, lg1, lg2, sign);
+    fft_cols_kernel<<<dim3(N2 / tc, batch), kThr, sm1, st>>>(in, tmp, lg1, lg2, sign, T);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_kernel(C);
-    fft_rows_kernel<<<dim3(N1 / tr, batch), kThr, sm2, st>>>(tmp, out, lg1, lg2, sign);
+    fft_rows_kernel<<<dim3(N1 / tr, batch), kThr, sm2, st>>>(tmp, out, lg1, lg2, sign, T);
     return cudaGetLastError();
 }
 
-size_t embed_ws(const Context &C, uint32_t batch) { return 2 * (size_t)batch * C.N * sizeof(double2); }
+size_t embed_ws(const Context &C, uint32_t batch) { return (2 * (size_t)batch + 2) * C.N * sizeof(double2); }
+
+// the roots table at the end of the workspace, filled on `st`
+cudaError_t roots(const Context &C, double2 *T, cudaStream_t st) {
+    count_kernel(C);
+    roots_kernel<<<(2 * C.N + kThr - 1) / kThr, kThr, 0, st>>>(T, C.N);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -199,13 +221,17 @@ int ckks_encode(ckks_context *ctx, const double *z, uint32_t batch, double scale
     cudaStream_t st = (cudaStream_t)stream;
     double2 *A = (double2 *)workspace;
     double2 *Bf = A + (size_t)batch * C.N;
-    count_kernel(C);
-    scatter_kernel<<<dim3((C.N / 2 + kThr - 1) / kThr, batch), kThr, 0, st>>>(z, A, C.N, scale);
-    cudaError_t err = cudaGetLastError();
-    if (err == cudaSuccess) err = dft(C, A, Bf, A, (int)batch, -1, st);
+    double2 *T = Bf + (size_t)batch * C.N;
+    cudaError_t err = roots(C, T, st);
     if (err == cudaSuccess) {
         count_kernel(C);
-        untwist_round_kernel<<<dim3((C.N + kThr - 1) / kThr, batch), kThr, 0, st>>>(A, (long long *)m, C.N);
+        scatter_kernel<<<dim3((C.N / 2 + kThr - 1) / kThr, batch), kThr, 0, st>>>(z, A, C.N, scale);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = dft(C, A, Bf, A, (int)batch, -1, T, st);
+    if (err == cudaSuccess) {
+        count_kernel(C);
+        untwist_round_kernel<<<dim3((C.N + kThr - 1) / kThr, batch), kThr, 0, st>>>(A, (long long *)m, C.N, T);
         err = cudaGetLastError();
     }
     if (err != cudaSuccess) {
@@ -225,13 +251,14 @@ int ckks_decode(ckks_context *ctx, const double *m, uint32_t batch, double scale
     cudaStream_t st = (cudaStream_t)stream;
     double2 *A = (double2 *)workspace;
     double2 *Bf = A + (size_t)batch * C.N;
-    cudaError_t err = cudaSuccess;
-    {
+    double2 *T = Bf + (size_t)batch * C.N;
+    cudaError_t err = roots(C, T, st);
+    if (err == cudaSuccess) {
         count_kernel(C);
-        twist_kernel<<<dim3((C.N + kThr - 1) / kThr, batch), kThr, 0, st>>>(m, A, C.N);
+        twist_kernel<<<dim3((C.N + kThr - 1) / kThr, batch), kThr, 0, st>>>(m, A, C.N, T);
         err = cudaGetLastError();
     }
-    if (err == cudaSuccess) err = dft(C, A, Bf, A, (int)batch, +1, st);
+    if (err == cudaSuccess) err = dft(C, A, Bf, A, (int)batch, +1, T, st);
     if (err == cudaSuccess) {
         count_kernel(C);
         slots_kernel<<<dim3((C.N / 2 + kThr - 1) / kThr, batch), kThr, 0, st>>>(A, z, C.N, 1.0 / scale);
