@@ -371,7 +371,10 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
  * residues outside [0, q) in their inputs and after every stage (tensor
  * product, Algorithm 1 rescale, relinearisation, root rescale), then
  * synchronise the stream and return CKKS_ECHECK if any were found (results
- * are still written); "nvtx" 1 = NVTX ranges around each stage's launches,
+ * are still written). The count lives in one word per context: checking
+ * calls (and ckks_check_residues, ckks_evk_verify) that run at the same
+ * time on one context, on different streams, share it and may report each
+ * other's violations. "nvtx" 1 = NVTX ranges around each stage's launches,
  * for profilers that filter by range. Both default to 0. */
 int ckks_tune_set(ckks_context *ctx, const char *key, int value);
 int ckks_tune_get(const ckks_context *ctx, const char *key, int *value);
