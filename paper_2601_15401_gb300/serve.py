@@ -41,6 +41,7 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     error: str | None = None
+    batch: int = -1          # id of the batch that ran it
     slots: object = None     # plaintext requests: [k][N/2] complex slot vectors (cts unused)
     seed: int = 0            # plaintext requests: seed of the encryption noise
 
@@ -151,6 +152,7 @@ class Scheduler:
             self.next_bid += 1
             for r in reqs:
                 r.admitted = now
+                r.batch = b.bid
             b.launched = now
             b.handle = self.be.launch(b)
             self.in_use += fp
@@ -490,6 +492,11 @@ def main():
     ap.add_argument("--plaintext", action="store_true",
                     help="requests carry slot vectors: encode, encrypt, multiply, decrypt, decode on the device")
     ap.add_argument("--k-max", type=int, default=12)
+    ap.add_argument("--jsonl", default=None, help="write one JSON line per completed request to this file")
+    ap.add_argument("--warmup-seconds", type=float, default=3.0,
+                    help="untimed serving at the same rate first: the first launch of each (N, k, level, batch) "
+                         "shape pays one-time costs (kernel loading, new allocator blocks) that otherwise "
+                         "queue up the opening seconds")
     ap.add_argument("--criterion", default="table2", choices=["table2", "precision"],
                     help="partitions: Table II, or the precision search's (smallest inner tuple degree)")
     args = ap.parse_args()
@@ -517,12 +524,20 @@ def main():
     budget = int(args.cap_gb * 1e9) - resident
     if budget <= 0:
         raise SystemExit(f"resident state ({resident / 1e9:.1f} GB) exceeds the cap")
-    warm = make(200.0, 0.2, args.seed + 1, log_ns)
+    warm = make(args.rate, args.warmup_seconds, args.seed + 1, log_ns)
     run_open_loop(Scheduler(be, budget, args.max_batch), warm)
     reqs = make(args.rate, args.seconds, args.seed, log_ns)
     sched = Scheduler(be, budget, args.max_batch)
     wall = run_open_loop(sched, reqs, timeout=args.seconds * 20 + 120)
     stats = latency_stats(sched.completed)
+    if args.jsonl:
+        t0 = min(r.arrival for r in reqs)
+        with open(args.jsonl, "w") as f:
+            for r in sorted(sched.completed, key=lambda r: r.arrival):
+                f.write(json.dumps({"rid": r.rid, "log_n": r.log_n, "k": r.k, "level": r.level, "batch": r.batch,
+                                    "arrival_s": round(r.arrival - t0, 6), "admitted_s": round(r.admitted - t0, 6),
+                                    "done_s": round(r.done - t0, 6),
+                                    "latency_ms": round((r.done - r.arrival) * 1e3, 3)}) + "\n")
     extra = {}
     if args.plaintext:
         import numpy as np
@@ -533,7 +548,8 @@ def main():
         extra = {"mode": "plaintext in / plaintext out", "max_abs_slot_error_per_k": dict(sorted(err.items())),
                  "secret": f"Hamming weight {h}" if h else "uniform ternary", "partitions": args.criterion}
     print(json.dumps({"metric": "served k-input ct-mults/s (Poisson arrivals, mixed k, N, level)",
-                      "offered_rate": args.rate, "seconds": args.seconds, "requests": len(reqs),
+                      "offered_rate": args.rate, "seconds": args.seconds, "warmup_seconds": args.warmup_seconds,
+                      "requests": len(reqs),
                       "completed": len(sched.completed), "wall_s": round(wall, 3),
                       "sustained_ctmults_s": round(len(sched.completed) / wall, 1), "latency": stats,
                       "batches": sched.admitted_batches, "mean_batch": round(len(reqs) / max(1, sched.admitted_batches), 2),
