@@ -446,7 +446,8 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     torch.cuda.synchronize()
     t0.record(copy)
     for c, cs in enumerate(copies):
-        cs.wait_event(t0) if c else None
+        if c:
+            cs.wait_event(t0)
         with torch.cuda.stream(cs):
             for k in ks:
                 for b in range(c, B, len(copies)):
