@@ -349,7 +349,9 @@ int ckks_profile_enable(ckks_context *ctx, int enable);
 int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, uint32_t *n_out);
 
 /* Launch tunables of a context; results are the same for every value.
- * Chosen by the autotuner: "ntt_tile" = elements per NTT tile (1024..8192,
+ * Chosen by the autotuner: "ntt_tile_cols" / "ntt_tile_blocks" = elements
+ * per CTA tile of the NTT's column / block phases ("ntt_tile" sets both;
+ * reading it gives the column value) (1024..8192,
  * power of two; default 4096), "bconv_threads" = threads per BConv block
  * (64..1024, multiple of 32; default 256), "mac_threads" = threads per
  * key-MAC block (same range).

@@ -695,7 +695,12 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
 
 static int *tune_slot(ckks_context *ctx, const char *key, int &lo, int &hi) {
     if (!ctx || !key) return nullptr;
-    if (!strcmp(key, "ntt_tile")) { lo = 1024; hi = 8192; return &ctx->c.tune_ntt_tile; }
+    if (!strcmp(key, "ntt_tile") || !strcmp(key, "ntt_tile_cols")) {
+        lo = 1024;
+        hi = 8192;
+        return &ctx->c.tune_ntt_tile_cols;
+    }
+    if (!strcmp(key, "ntt_tile_blocks")) { lo = 1024; hi = 8192; return &ctx->c.tune_ntt_tile_blocks; }
     if (!strcmp(key, "bconv_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_bconv_threads; }
     if (!strcmp(key, "mac_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_mac_threads; }
     if (!strcmp(key, "inner_rescale")) { lo = 0; hi = 2; return &ctx->c.tune_inner_rescale; }
@@ -710,9 +715,10 @@ int ckks_tune_set(ckks_context *ctx, const char *key, int value) {
     int lo, hi;
     int *slot = tune_slot(ctx, key, lo, hi);
     if (!slot || value < lo || value > hi) return CKKS_EINVAL;
-    if (!strcmp(key, "ntt_tile") && (value & (value - 1))) return CKKS_EINVAL;
+    if (!strncmp(key, "ntt_tile", 8) && (value & (value - 1))) return CKKS_EINVAL;
     if ((!strcmp(key, "bconv_threads") || !strcmp(key, "mac_threads")) && value % 32) return CKKS_EINVAL;
     *slot = value;
+    if (!strcmp(key, "ntt_tile")) ctx->c.tune_ntt_tile_blocks = value;  // both phases
     return CKKS_OK;
 }
 

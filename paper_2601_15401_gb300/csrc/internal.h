@@ -120,7 +120,8 @@ struct Context {
     std::atomic<int> sticky{0};
     Profiler prof;
     // launch tunables
-    int tune_ntt_tile = 4096;
+    int tune_ntt_tile_cols = 4096;    // elements per CTA tile, column phases
+    int tune_ntt_tile_blocks = 4096;  // elements per CTA tile, block phases
     int tune_bconv_threads = 256;
     int tune_mac_threads = 256;
     // forms of the rescaling (same results; for measuring the paper's

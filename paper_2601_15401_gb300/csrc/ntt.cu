@@ -415,14 +415,14 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
     if (cols) {
         logn = log_n1;
         int n = 1 << logn;
-        n_sub = C.tune_ntt_tile / n;
+        n_sub = C.tune_ntt_tile_cols / n;
         if (n_sub > P.N2) n_sub = P.N2;
         tiles = P.N2 / n_sub;
         smem = (size_t)n * n_sub * sizeof(u64);
     } else {
         logn = log_n2;
         int n = 1 << logn;
-        n_sub = C.tune_ntt_tile / n;
+        n_sub = C.tune_ntt_tile_blocks / n;
         if (n_sub < 1) n_sub = 1;
         if (n_sub > P.N1) n_sub = P.N1;
         tiles = P.N1 / n_sub;

@@ -167,7 +167,8 @@ def one_per_launch(contexts, requests, executor: BatchExecutor):
 # autotuner
 # ---------------------------------------------------------------------------
 TUNE_SPACE = {
-    "ntt_tile": [2048, 4096, 8192],
+    "ntt_tile_cols": [2048, 4096, 8192],
+    "ntt_tile_blocks": [1024, 2048, 4096],
     "bconv_threads": [128, 256, 512],
     "mac_threads": [128, 256, 512],
 }
