@@ -268,6 +268,27 @@ int ckks_mul_k(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, const ckks_e
 int ckks_mul_k_batch(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uint32_t batch, const ckks_evk_set *evk,
                      const ckks_plan *plan, ckks_tuple *out, void *workspace, size_t ws_bytes, void *stream);
 
+/* Uneven work in one call (Section V: products of different k, partitions
+ * and levels): each request is one ckks_mul_k_batch group (same k, plan and
+ * level inside it, its own batch stride). ckks_mul_k_requests enqueues the
+ * groups in order on `stream`, reusing one workspace of
+ * ckks_requests_workspace_size bytes (the largest group's need); it
+ * allocates nothing and does not synchronise (unless the "check_residues"
+ * tunable is on). On an error it returns that group's code and *done (if
+ * not NULL) gives the number of groups enqueued before it. The Python
+ * executor builds such groups from arbitrary requests and replays them from
+ * a CUDA graph over several streams. */
+typedef struct {
+    const ckks_tuple *ct;       /* [batch][k] input tuples */
+    uint32_t k, batch;
+    const ckks_evk_set *evk;
+    const ckks_plan *plan;      /* partition tree for k inputs */
+    ckks_tuple *out;            /* [batch] outputs */
+} ckks_request;
+int ckks_requests_workspace_size(const ckks_context *ctx, const ckks_request *req, uint32_t n, size_t *bytes);
+int ckks_mul_k_requests(ckks_context *ctx, const ckks_request *req, uint32_t n, uint32_t *done, void *workspace,
+                        size_t ws_bytes, void *stream);
+
 /* ckks_mul2: the standard 2-input multiply of Section II (Eq. 1-7): tensor
  * product, relinearisation with ModDown finished in the NTT domain, one RS in
  * the NTT domain (Eq. 7). The comparator for chained multiplication. Output
@@ -303,6 +324,10 @@ int ckks_rescale_workspace_size(const ckks_context *ctx, uint32_t n_polys, uint3
                                 size_t *bytes);
 int ckks_rescale_multi(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckks_tuple *out, void *workspace,
                        size_t ws_bytes, void *stream);
+/* ckks_rescale (Eq. 7): one rescale of every polynomial, NTT domain in and
+ * out (level - 1); ckks_rescale_multi with mu = 1, same workspace rule. */
+int ckks_rescale(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *workspace, size_t ws_bytes,
+                 void *stream);
 
 /* ckks_rescale_multi_noalloc: the same result as ckks_rescale_multi, for
  * callers that cannot allocate device memory where they need a rescale
@@ -320,6 +345,7 @@ int ckks_rescale_multi(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckk
  * the GPU (different streams, or different host threads) race and must be
  * ordered by the caller. Keep the timing hook off during these calls. */
 size_t ckks_rescale_noalloc_capacity(void);
+
 int ckks_rescale_multi_noalloc(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckks_tuple *out, void *stream);
 
 /* Forward / inverse transform of every limb of a tuple (in and out may be

@@ -44,6 +44,11 @@ class _Tuple(ctypes.Structure):
                 ("poly_stride", ctypes.c_uint32), ("ntt_form", ctypes.c_uint32), ("scale", ctypes.c_double)]
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("ct", ctypes.c_void_p), ("k", ctypes.c_uint32), ("batch", ctypes.c_uint32),
+                ("evk", ctypes.c_void_p), ("plan", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
 class _KStats(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
                 ("alg_bytes", ctypes.c_double)]
@@ -332,6 +337,45 @@ class Context:
         for o, r in zip(outs, oarr):
             o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride = r.level, r.n_polys, r.ntt_form, r.scale, r.poly_stride
         return outs
+
+    def _requests(self, groups, evk):
+        """groups: list of (cts [batch][k] Tuples, outs [batch] Tuples, partition or None)."""
+        keep, reqs = [], []
+        for cts, outs, part in groups:
+            k = len(cts[0])
+            arr = (_Tuple * (len(cts) * k))(*[c.c() for row in cts for c in row])
+            oarr = (_Tuple * len(outs))(*[o.c() for o in outs])
+            keep.append((arr, oarr, outs))
+            reqs.append(_Request(ctypes.cast(arr, ctypes.c_void_p), k, len(cts), evk._h, self.plan(k, part),
+                                 ctypes.cast(oarr, ctypes.c_void_p)))
+        return (_Request * len(reqs))(*reqs), keep
+
+    def requests_workspace_size(self, groups, evk) -> int:
+        rr, _ = self._requests(groups, evk)
+        n = ctypes.c_size_t()
+        _check(lib().ckks_requests_workspace_size(self._h, rr, len(groups), ctypes.byref(n)),
+               "ckks_requests_workspace_size")
+        return n.value
+
+    def mul_k_requests(self, groups, evk, workspace, stream=None) -> int:
+        """Uneven groups of k-input products in one call (see the header);
+        returns the number of groups enqueued."""
+        rr, keep = self._requests(groups, evk)
+        done = ctypes.c_uint32()
+        _check(lib().ckks_mul_k_requests(self._h, rr, len(groups), ctypes.byref(done), workspace.data_ptr(),
+                                         workspace.numel() * workspace.element_size(), _stream(stream)),
+               "ckks_mul_k_requests")
+        for arr, oarr, outs in keep:
+            for o, r in zip(outs, oarr):
+                o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride = r.level, r.n_polys, r.ntt_form, r.scale, r.poly_stride
+        return done.value
+
+    def rescale(self, t: Tuple, out: Tuple, workspace, stream=None) -> Tuple:
+        c, o = t.c(), out.c()
+        _check(lib().ckks_rescale(self._h, ctypes.byref(c), ctypes.byref(o), workspace.data_ptr(),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)), "ckks_rescale")
+        out.level, out.n_polys, out.ntt_form, out.scale, out.poly_stride = o.level, o.n_polys, o.ntt_form, o.scale, o.poly_stride
+        return out
 
     def mul2_workspace_size(self, level: int, batch: int = 1) -> int:
         v = ctypes.c_size_t()

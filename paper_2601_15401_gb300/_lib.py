@@ -38,6 +38,9 @@ SIGNATURES = {
     "ckks_rotate": [V, V, U32, V, V, V, SZ, V],
     "ckks_rotate_batch": [V, V, U32, U32, V, V, V, SZ, V],
     "ckks_evk_verify": [V, V],
+    "ckks_rescale": [V, V, V, V, SZ, V],
+    "ckks_requests_workspace_size": [V, V, U32, V],
+    "ckks_mul_k_requests": [V, V, U32, V, V, SZ, V],
     "ckks_check_residues": [V, V, V, V],
     "ckks_encrypt_workspace_size": [V, V],
     "ckks_encrypt_batch_workspace_size": [V, U32, U32, V],

@@ -333,6 +333,33 @@ int ckks_mul_k_batch(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uint32
     return mul_k_common(ctx, ct, k, batch, evk, plan, out, workspace, ws_bytes, stream);
 }
 
+int ckks_requests_workspace_size(const ckks_context *ctx, const ckks_request *req, uint32_t n, size_t *bytes) {
+    if (!ctx || !req || !bytes || n < 1) return CKKS_EINVAL;
+    size_t need = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const ckks_request &r = req[i];
+        if (!r.ct || !r.plan || r.batch < 1 || (int)r.k != r.plan->p.k) return CKKS_EINVAL;
+        const uint32_t level = r.ct[0].level;
+        if (level <= (uint32_t)r.plan->p.depth || level > (uint32_t)ctx->c.L) return CKKS_ELEVEL;
+        need = std::max(need, mul_k_ws_bytes(ctx->c, r.plan->p, (int)level, (int)r.batch));
+    }
+    *bytes = need;
+    return CKKS_OK;
+}
+
+int ckks_mul_k_requests(ckks_context *ctx, const ckks_request *req, uint32_t n, uint32_t *done, void *workspace,
+                        size_t ws_bytes, void *stream) {
+    if (done) *done = 0;
+    if (!ctx || !req || n < 1) return CKKS_EINVAL;
+    for (uint32_t i = 0; i < n; ++i) {
+        const ckks_request &r = req[i];
+        const int rc = mul_k_common(ctx, r.ct, r.k, r.batch, r.evk, r.plan, r.out, workspace, ws_bytes, stream);
+        if (rc != CKKS_OK) return rc;
+        if (done) *done = i + 1;
+    }
+    return CKKS_OK;
+}
+
 // batch stride of a [batch] tuple array; -1 if the pointers are not evenly spaced
 static i64 batch_stride(const ckks_tuple *t, uint32_t batch) {
     i64 bs = batch > 1 ? (i64)(t[1].data - t[0].data) : 0;
@@ -607,6 +634,11 @@ int ckks_rescale_multi(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckk
     out->ntt_form = 1;
     out->scale = scale;
     return CKKS_OK;
+}
+
+int ckks_rescale(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *workspace, size_t ws_bytes,
+                 void *stream) {
+    return ckks_rescale_multi(ctx, in, 1, out, workspace, ws_bytes, stream);
 }
 
 static int transform_api(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *stream, bool fwd) {
