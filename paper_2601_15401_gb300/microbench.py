@@ -26,7 +26,7 @@ def main():
     import synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "rotate", "encode", "decode", "precision"], default="ntt")
+    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "chain3", "rotate", "encode", "decode", "precision"], default="ntt")
     ap.add_argument("--log-n", type=int, default=16)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--k", type=int, default=8)
@@ -34,6 +34,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--tune", action="append", default=[], help="key=value library tunable")
     ap.add_argument("--partition", default=None, help="partition text for --op mul_k (default Table II)")
+    ap.add_argument("--params", default="large", choices=["large", "mid"],
+                    help="large: 24 x 50-bit q, 8 x 60-bit p, dnum 3; mid: q_0 60-bit + 11 x 45-bit, 4 x 60-bit p, dnum 3")
     ap.add_argument("--secret-h", type=int, default=0, help="--op precision: Hamming weight of s (0: uniform)")
     ap.add_argument("--scale-bits", type=int, default=50, help="--op precision: log2 of the encoding scale")
     ap.add_argument("--criterion", default="table2", choices=["table2", "precision"],
@@ -41,7 +43,7 @@ def main():
     args = ap.parse_args()
     if args.op == "precision":
         return precision(args)
-    p = synth.params_large(log_n=args.log_n)
+    p = synth.params_mid(log_n=args.log_n) if args.params == "mid" else synth.params_large(log_n=args.log_n)
     ctx = G.Context.from_params(p)
     L, N, B = p.L, p.N, args.batch
     for kv in args.tune:
@@ -110,6 +112,21 @@ def main():
 
             def run():
                 ctx.mul_k_batch(tup, evk, outs, ws, partition=args.partition)
+        elif args.op == "chain3":
+            # three inputs through two standard 2-input multiplies: (a b) c
+            inp = synth.uniform_residues_torch(p.q, (B, 3, 2), N, 14, "cuda")
+            ab = torch.empty((B, 2, L - 1, N), dtype=torch.uint64, device="cuda")
+            out = torch.empty((B, 2, L - 2, N), dtype=torch.uint64, device="cuda")
+            a_ = [G.Tuple(inp[b, 0], 2, L, L) for b in range(B)]
+            b_ = [G.Tuple(inp[b, 1], 2, L, L) for b in range(B)]
+            c_ = [G.Tuple(inp[b, 2], 2, L, L) for b in range(B)]
+            abt = [G.Tuple(ab[b], 2, L - 1, L - 1) for b in range(B)]
+            outs = [G.Tuple(out[b], 2, L - 2, L - 2) for b in range(B)]
+            ws = torch.empty(ctx.mul2_workspace_size(L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
+
+            def run():
+                ctx.mul2_batch(a_, b_, evk, abt, ws)
+                ctx.mul2_batch(abt, c_, evk, outs, ws)
         else:
             inp = synth.uniform_residues_torch(p.q, (B, 2, 2), N, 12, "cuda")
             out = torch.empty((B, 2, L - 1, N), dtype=torch.uint64, device="cuda")
