@@ -34,8 +34,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--tune", action="append", default=[], help="key=value library tunable")
     ap.add_argument("--partition", default=None, help="partition text for --op mul_k (default Table II)")
-    ap.add_argument("--params", default="large", choices=["large", "mid"],
-                    help="large: 24 x 50-bit q, 8 x 60-bit p, dnum 3; mid: q_0 60-bit + 11 x 45-bit, 4 x 60-bit p, dnum 3")
+    ap.add_argument("--params", default="large", choices=["large", "mid", "small"],
+                    help="large: 24 x 50-bit q, 8 x 60-bit p, dnum 3; mid: q_0 60-bit + 11 x 45-bit, 4 x 60-bit p, "
+                         "dnum 3; small: 4 x 50-bit q, one 60-bit p, dnum 1")
+    ap.add_argument("--graph", action="store_true", help="capture one rep in a CUDA graph and time its replays")
+    ap.add_argument("--latency", action="store_true",
+                    help="also time each rep alone on the host (launch to completion, synchronised)")
     ap.add_argument("--secret-h", type=int, default=0, help="--op precision: Hamming weight of s (0: uniform)")
     ap.add_argument("--scale-bits", type=int, default=50, help="--op precision: log2 of the encoding scale")
     ap.add_argument("--criterion", default="table2", choices=["table2", "precision"],
@@ -43,7 +47,12 @@ def main():
     args = ap.parse_args()
     if args.op == "precision":
         return precision(args)
-    p = synth.params_mid(log_n=args.log_n) if args.params == "mid" else synth.params_large(log_n=args.log_n)
+    if args.params == "small":
+        p = synth.params_small(log_n=args.log_n)
+    elif args.params == "mid":
+        p = synth.params_mid(log_n=args.log_n)
+    else:
+        p = synth.params_large(log_n=args.log_n)
     ctx = G.Context.from_params(p)
     L, N, B = p.L, p.N, args.batch
     for kv in args.tune:
@@ -140,19 +149,46 @@ def main():
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize()
+    step = run
+    if args.graph:
+        import time as _t
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            run()  # one eager pass on the capture stream first
+            side.synchronize()
+            with torch.cuda.graph(graph, stream=side):
+                run()
+        torch.cuda.synchronize()
+
+        def step():
+            graph.replay()
     ctx.counters(reset=True)
-    ctx.profile(True)
+    ctx.profile(not args.graph)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.reps):
-        run()
+        step()
     e1.record()
     e1.synchronize()
     ctx.profile(False)
-    prof = ctx.profile_read()
+    prof = ctx.profile_read() if not args.graph else {}
+    latency = None
+    if args.latency:
+        import time as _t
+        lat = []
+        for _ in range(max(20, args.reps)):
+            t = _t.perf_counter()
+            step()
+            torch.cuda.synchronize()
+            lat.append((_t.perf_counter() - t) * 1e3)
+        lat.sort()
+        latency = {"p50_ms": round(lat[len(lat) // 2], 4), "min_ms": round(lat[0], 4), "n": len(lat)}
     ctx.check()
     print(json.dumps({
-        "op": args.op, "log_n": args.log_n, "batch": B, "k": args.k, "tune": args.tune, "partition": args.partition,
+        "op": args.op, "params": args.params, "log_n": args.log_n, "batch": B, "k": args.k, "tune": args.tune,
+        "partition": args.partition, "graph": args.graph, "latency": latency,
         "ms_per_rep": round(e0.elapsed_time(e1) / args.reps, 4), "counters_per_rep": {n: v // args.reps for n, v in ctx.counters().items()},
         "kernels": {n: {"launches": v["launches"], "avg_us": round(v["total_ms"] * 1e3 / v["launches"], 2),
                         "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)} for n, v in prof.items()}}))
