@@ -86,3 +86,41 @@ def test_encrypt_decrypt_batch_match_single_and_oracle():
             lv = min(level, 2)
             want = O.decrypt(octx, got[b][:, :lv], km.s)
             np.testing.assert_allclose(dec[b].cpu().numpy(), np.array([float(x) for x in want]), rtol=1e-15, atol=0)
+
+
+@pytest.mark.slow
+def test_encrypt_decrypt_batch_full_size():
+    """N = 2^16, L = 24: batched encryption equals the oracle's on every
+    residue of two messages; decryption equals the oracle's two-limb lift."""
+    import paper_2601_15401_gb300 as G
+    params = synth.params_large()
+    ctx = G.Context.from_params(params)
+    octx = O.Ctx(params)
+    km = synth.key_material(params, 2, 91)
+    s = torch.from_numpy(km.s).cuda()
+    pa, pe = synth.public_key_draw(params, 91)
+    ws1 = torch.empty(ctx.encrypt_workspace_size() // 8, dtype=torch.uint64, device="cuda")
+    pk = torch.empty((2, params.L, params.N), dtype=torch.uint64, device="cuda")
+    ctx.public_key(s, dev(pa), torch.from_numpy(pe).cuda(), pk, ws1)
+    opk = O.public_key(octx, km.s, pa, pe)
+    assert np.array_equal(host(pk), np.stack(opk))
+    N, L, B = params.N, params.L, 2
+    draws = [synth.encryption_draw(params, 92, b) for b in range(B)]
+    # any integer message (the oracle's O(N^2) encoder is too slow at this N)
+    m = np.stack([synth.rng(93, b).integers(-2 ** 40, 2 ** 40, N) for b in range(B)]).astype(np.int64)
+    cols = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in
+            (m, np.stack([d.v for d in draws]), np.stack([d.e0 for d in draws]), np.stack([d.e1 for d in draws]))]
+    out = torch.zeros((B, 2, L, N), dtype=torch.uint64, device="cuda")
+    outs = [G.Tuple.wrap(out[b]) for b in range(B)]
+    ws = torch.empty(ctx.encrypt_batch_workspace_size(L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
+    ctx.encrypt_batch(*cols, pk, L, outs, ws)
+    got = host(out)
+    for b, d in enumerate(draws):
+        want = O.encrypt(octx, [int(x) for x in m[b]], opk, d.v, d.e0, d.e1)
+        assert np.array_equal(got[b], want), b
+    dec = torch.empty((B, N), dtype=torch.float64, device="cuda")
+    dws = torch.empty(ctx.decrypt_batch_workspace_size(B) // 8 + 1, dtype=torch.uint64, device="cuda")
+    ctx.decrypt_batch(outs, s, dec, dws)
+    for b in range(B):
+        want = O.decrypt(octx, got[b][:, :2], km.s)
+        np.testing.assert_allclose(dec[b].cpu().numpy(), np.array([float(x) for x in want]), rtol=1e-15, atol=0)
