@@ -91,8 +91,11 @@ def test_encrypt_decrypt_batch_match_single_and_oracle():
 @pytest.mark.slow
 def test_encrypt_decrypt_batch_full_size():
     """N = 2^16, L = 24: batched encryption equals the oracle's on every
-    residue of two messages; decryption equals the oracle's two-limb lift."""
+    residue; decryption equals c_0 + c_1 s formed from oracle steps (the
+    product in the NTT domain, pinned by the convolution theorem, then the
+    inverse transform and a two-prime CRT)."""
     import paper_2601_15401_gb300 as G
+    from oracle import ring
     params = synth.params_large()
     ctx = G.Context.from_params(params)
     octx = O.Ctx(params)
@@ -104,23 +107,22 @@ def test_encrypt_decrypt_batch_full_size():
     ctx.public_key(s, dev(pa), torch.from_numpy(pe).cuda(), pk, ws1)
     opk = O.public_key(octx, km.s, pa, pe)
     assert np.array_equal(host(pk), np.stack(opk))
-    N, L, B = params.N, params.L, 2
-    draws = [synth.encryption_draw(params, 92, b) for b in range(B)]
-    # any integer message (the oracle's O(N^2) encoder is too slow at this N)
-    m = np.stack([synth.rng(93, b).integers(-2 ** 40, 2 ** 40, N) for b in range(B)]).astype(np.int64)
-    cols = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in
-            (m, np.stack([d.v for d in draws]), np.stack([d.e0 for d in draws]), np.stack([d.e1 for d in draws]))]
-    out = torch.zeros((B, 2, L, N), dtype=torch.uint64, device="cuda")
-    outs = [G.Tuple.wrap(out[b]) for b in range(B)]
-    ws = torch.empty(ctx.encrypt_batch_workspace_size(L, B) // 8 + 1, dtype=torch.uint64, device="cuda")
+    N, L = params.N, params.L
+    d = synth.encryption_draw(params, 92, 0)
+    m = synth.rng(93, 0).integers(-2 ** 40, 2 ** 40, N).astype(np.int64)   # any integer message
+    cols = [torch.from_numpy(np.ascontiguousarray(x[None])).cuda() for x in (m, d.v, d.e0, d.e1)]
+    out = torch.zeros((1, 2, L, N), dtype=torch.uint64, device="cuda")
+    outs = [G.Tuple.wrap(out[0])]
+    ws = torch.empty(ctx.encrypt_batch_workspace_size(L, 1) // 8 + 1, dtype=torch.uint64, device="cuda")
     ctx.encrypt_batch(*cols, pk, L, outs, ws)
-    got = host(out)
-    for b, d in enumerate(draws):
-        want = O.encrypt(octx, [int(x) for x in m[b]], opk, d.v, d.e0, d.e1)
-        assert np.array_equal(got[b], want), b
-    dec = torch.empty((B, N), dtype=torch.float64, device="cuda")
-    dws = torch.empty(ctx.decrypt_batch_workspace_size(B) // 8 + 1, dtype=torch.uint64, device="cuda")
+    got = host(out)[0]
+    want = O.encrypt(octx, [int(x) for x in m], opk, d.v, d.e0, d.e1)
+    assert np.array_equal(got, want)
+    dec = torch.empty((1, N), dtype=torch.float64, device="cuda")
+    dws = torch.empty(ctx.decrypt_batch_workspace_size(1) // 8 + 1, dtype=torch.uint64, device="cuda")
     ctx.decrypt_batch(outs, s, dec, dws)
-    for b in range(B):
-        want = O.decrypt(octx, got[b][:, :2], km.s)
-        np.testing.assert_allclose(dec[b].cpu().numpy(), np.array([float(x) for x in want]), rtol=1e-15, atol=0)
+    q2 = octx.q[:2]
+    S2 = O.ntt_poly(np.stack([ring.from_signed(km.s, qj) for qj in q2]), q2)
+    P = O.intt_poly(ring.addmod_rows(got[0][:2], ring.mulmod_rows(got[1][:2], S2, q2), q2), q2)
+    want_dec = O.crt_centered(P, q2)
+    np.testing.assert_allclose(dec[0].cpu().numpy(), np.array([float(x) for x in want_dec]), rtol=1e-15, atol=0)
