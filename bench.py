@@ -396,16 +396,22 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     host_out = {k: torch.empty((B, 2, L - depth[k], N), dtype=torch.uint64, pin_memory=True) for k in ks}
     h2d = sum(B * k * 2 * L * N * 8 for k in ks)
     d2h = sum(B * 2 * (L - depth[k]) * N * 8 for k in ks)
-    # several copy streams: the batch elements' copies spread over them so
-    # that more than one copy engine moves data at a time
+    # uploads and downloads on their own streams: the next step's upload of
+    # k waits only for this step's multiply of k (which frees its input
+    # buffers), not for the downloads; several upload streams spread the
+    # batch elements' copies over copy engines when asked
     copies = [torch.cuda.Stream(device=dev) for _ in range(max(1, args.copy_streams))]
     copy = copies[0]
+    down = torch.cuda.Stream(device=dev)
+    used = {}  # k -> event: the last multiply that read dev_inp[k]
 
     def step():
         up = {}
         for k in ks:
             evs = []
             for c, cs in enumerate(copies):
+                if k in used:
+                    cs.wait_event(used[k])
                 with torch.cuda.stream(cs):
                     for b in range(c, B, len(copies)):
                         dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
@@ -419,15 +425,13 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
             ctx.mul_k_batch(tup[k], evk, otup[k], ws, stream=stream)
             done = torch.cuda.Event()
             done.record(stream)
-            for c, cs in enumerate(copies):
-                cs.wait_event(done)
-                with torch.cuda.stream(cs):
-                    for b in range(c, B, len(copies)):
-                        host_out[k][b].copy_(dev_out[k][b], non_blocking=True)
-        for cs in copies:
-            fin = torch.cuda.Event()
-            fin.record(cs)
-            stream.wait_event(fin)
+            used[k] = done
+            down.wait_event(done)
+            with torch.cuda.stream(down):
+                host_out[k].copy_(dev_out[k], non_blocking=True)
+        fin = torch.cuda.Event()
+        fin.record(down)
+        stream.wait_event(fin)
 
     for _ in range(max(1, args.warmup)):
         step()
@@ -462,7 +466,9 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     return {"value": round(B * len(ks) * world / (ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
             "h2d_GBps_alone": round(h2d / (t0.elapsed_time(t1) / 1e3) / 1e9, 1),
-            "copy_streams": len(copies), "overlap": "uploads on copy streams overlap the multiplies"}
+            "copy_streams": len(copies),
+            "overlap": "uploads (own stream) overlap the multiplies of this and the previous step; downloads on "
+                       "a second stream"}
 
 
 # ---------------------------------------------------------------------------
