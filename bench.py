@@ -217,6 +217,7 @@ def run_ours(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     ctx.check()
+    int_peaks = measure_int_peaks(G, params)
     barrier()
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -256,7 +257,7 @@ def run_ours(args, rank, world, local_rank):
     roofline = None
     if dom[0]:
         st = dom[1]
-        achieved = st["alg_bytes"] / (st["total_ms"] / 1e3) / 1e9
+        achieved_gbs = st["alg_bytes"] / (st["total_ms"] / 1e3) / 1e9
         traffic = None
         busy = None
         try:
@@ -269,18 +270,36 @@ def run_ours(args, rank, world, local_rank):
                 busy = ent.get("fmaheavy_busy")
         except Exception:
             pass
-        roofline = {"bound": "hbm", "kernel": dom[0], "achieved": round(achieved, 1), "peak": hbm_peak,
-                    "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+        unit_peak = int_peaks.get(op_unit(dom[0]))
+        achieved_ops = st["int_ops"] / (st["total_ms"] / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": dom[0],
+                    "achieved": round(achieved_ops, 2), "peak": round(unit_peak / 1e9, 2) if unit_peak else None,
+                    "unit": "G Shoup products/s" if dom[0].startswith("ntt") else "G 128-bit MACs/s",
+                    "frac": round(achieved_ops * 1e9 / unit_peak, 4) if unit_peak else None,
+                    "traffic": traffic,
+                    "peak_source": "measured in this run (ckks_peak_int: register-only stream of lazy NTT butterflies "
+                                   "/ 128-bit MACs over every SM, CUDA events, best of 5), the integer-multiply "
+                                   "roofline of this GPU for the operation the kernel is built from",
+                    "alg_ops_per_launch": st["int_ops"] / st["launches"],
                     "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
                     "avg_launch_us": st["total_ms"] * 1e3 / st["launches"],
+                    "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                            "frac": round(achieved_gbs / hbm_peak, 4),
+                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"},
                     "fmaheavy_busy": busy,
-                    "limiter": "integer multiply (fmaheavy) pipe, not HBM: ncu shows it 54-71 % busy in the NTT "
-                               "phases, about 14 of its instructions per 64-bit Shoup product, DRAM traffic equal "
-                               "to the algorithmic bytes (profiles/ntt_phase_pipes_N65536_batch8.md, traffic.json)"}
+                    "limiter": "integer multiply (fmaheavy) pipe, not HBM: ncu shows it 54-75 % busy in the NTT "
+                               "phases with math-pipe throttle the top stall, about 14 of its instructions per "
+                               "64-bit Shoup product, DRAM at 23-28 % and traffic equal to the algorithmic bytes "
+                               "(profiles/ntt_phase_pipes_N65536_batch8.md, ntt_phase_N65536_batch16.md)"}
+    def int_frac(n, v):
+        pk = int_peaks.get(op_unit(n))
+        return round(v["int_ops"] / (v["total_ms"] / 1e3) / pk, 4) if pk and v["int_ops"] else None
+
     kernel_table = {n: {"launches": v["launches"] // args.steps, "ms_per_step": round(v["total_ms"] / args.steps, 3),
                         "share": round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4),
-                        "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)}
+                        "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1),
+                        "hbm_frac": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9 / hbm_peak, 4),
+                        "int_frac": int_frac(n, v)}
                     for n, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])}
     # whole-step algorithmic bytes: inputs + outputs + keys once per step
     in_bytes = sum(B * k * 2 * L * N * 8 for k in ks)
@@ -307,6 +326,7 @@ def run_ours(args, rank, world, local_rank):
         "per_k": per_k,
         "clocks": clk,
         "tuning": tuned,
+        "int_peaks_Gops": {k: round(v / 1e9, 2) for k, v in int_peaks.items()},
     }
 
     # ---------------- comparators (outside the timed region)
@@ -348,6 +368,26 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
+def op_unit(kernel_class: str) -> str:
+    """The integer operation a kernel class is built from (its roofline unit)."""
+    if kernel_class.startswith("ntt"):
+        return "butterfly"
+    if kernel_class in ("bconv", "mac"):
+        return "mac128"
+    return ""
+
+
+def measure_int_peaks(G, params) -> dict:
+    """Rate of the lazy NTT butterfly and of the 128-bit MAC on this GPU
+    (register-only kernels over every SM; operations/s), taken at the same
+    point of the run as the timed steps."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    q = int(params.q[0])
+    return {u: max(G.peak_int(u, q, blocks=sms * per_sm, threads=256, iters=2048) for per_sm in (8, 16))
+            for u in ("butterfly", "mac128")}
+
+
 def chained_ms(ctx, evk, inp, k, B, L, N, dev, stream, reps):
     """Time the binary tree of standard 2-input multiplies over the batch."""
     import torch
@@ -387,6 +427,39 @@ def chained_ms(ctx, evk, inp, k, B, L, N, dev, stream, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def _cpulist(text: str) -> set:
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        a, _, b = part.partition("-")
+        cpus.update(range(int(a), int(b or a) + 1))
+    return cpus
+
+
+def gpu_local_cpus(index: int) -> dict:
+    """The GPU's PCI NUMA node and the CPUs local to it (sysfs, via the bus
+    id nvidia-smi reports), restricted to the CPUs this process may use."""
+    info = {"gpu_numa_node": None, "cpus": None}
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        dev = f"/sys/bus/pci/devices/{dom[-4:].lower()}:{rest.lower()}"
+        info["pci"] = os.path.basename(dev)
+        info["gpu_numa_node"] = int(open(os.path.join(dev, "numa_node")).read().strip())
+        local = _cpulist(open(os.path.join(dev, "local_cpulist")).read())
+        allowed = os.sched_getaffinity(0)
+        usable = local & allowed
+        info["local_cpus"] = len(local)
+        info["allowed_cpus"] = len(allowed)
+        if usable and usable != allowed:
+            info["cpus"] = usable
+    except Exception as e:  # no sysfs entry (container) or no nvidia-smi: leave placement to the OS
+        info["error"] = type(e).__name__
+    return info
+
+
 def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp, dev_out, tup, otup, src):
     """The step through the C ABI with host buffers: every k's inputs are
     copied from pinned host memory, multiplied, and the outputs copied back,
@@ -396,9 +469,17 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     second stream after their multiply."""
     import torch
     kmax = max(ks)
+    # pinned host buffers on the GPU's own NUMA node: allocate them from a
+    # thread bound to the CPUs local to the GPU (first touch places the pages)
+    numa = gpu_local_cpus(dev.index if dev.index is not None else 0)
+    prev_affinity = os.sched_getaffinity(0)
+    if numa.get("cpus"):
+        os.sched_setaffinity(0, numa["cpus"])
     host_in = torch.empty((B, kmax, 2, L, N), dtype=torch.uint64, pin_memory=True)
     host_in.copy_(src)  # the step's synthetic inputs, staged in pinned host memory
     host_out = {k: torch.empty((B, 2, L - depth[k], N), dtype=torch.uint64, pin_memory=True) for k in ks}
+    numa_note = {k: v for k, v in numa.items() if k != "cpus"}
+    numa_note["bound_cpus"] = len(numa["cpus"]) if numa.get("cpus") else None
     h2d = sum(B * k * 2 * L * N * 8 for k in ks)
     d2h = sum(B * 2 * (L - depth[k]) * N * 8 for k in ks)
     # uploads and downloads on their own streams: the next step's upload of
@@ -472,11 +553,12 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     ms = e0.elapsed_time(e1) / steps
     ms = reduce_max(ms, world, dev)
     bw_after = upload_alone()
+    os.sched_setaffinity(0, prev_affinity)
     ctx.check()
     return {"value": round(B * len(ks) * world / (ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
             "h2d_GBps_alone": [round(bw_before, 1), round(bw_after, 1)],
-            "copy_streams": len(copies),
+            "copy_streams": len(copies), "host_numa": numa_note,
             "overlap": "uploads (own stream) overlap the multiplies of this and the previous step; downloads on "
                        "a second stream"}
 

@@ -329,21 +329,26 @@ int ckks_rescale_multi(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckk
 int ckks_rescale(ckks_context *ctx, const ckks_tuple *in, ckks_tuple *out, void *workspace, size_t ws_bytes,
                  void *stream);
 
-/* ckks_rescale_multi_noalloc: the same result as ckks_rescale_multi, for
- * callers that cannot allocate device memory where they need a rescale
- * (inside someone else's stream capture, in a loop that forbids allocator
- * calls, or in a component that only receives device pointers). The paper
- * has no counterpart: this is an interface for such callers. Its scratch is
- * a fixed device array inside the library, ckks_rescale_noalloc_capacity()
- * bytes (32 MiB), held on every device that loads the library until exit;
- * the call makes no cudaMalloc / cudaFree or other allocation. Inputs and
- * outputs are still the caller's (in and out may be the same tuple).
- * The first call on a device resolves the array's device address (once per
- * device, that device made current); make that first call before any stream
- * capture. Sizes whose scratch exceeds the capacity are rejected with
- * CKKS_ENOMEM. All calls share the one array: calls whose work overlaps on
- * the GPU (different streams, or different host threads) race and must be
- * ordered by the caller. Keep the timing hook off during these calls. */
+/* ckks_rescale_multi_noalloc: the result of ckks_rescale_multi (Algorithm 1,
+ * always that form, whatever the context's "inner_rescale" setting), for
+ * callers that cannot allocate device memory where they need a rescale: a
+ * component that only receives device pointers from another one and has no
+ * allocator of its own, or a loop that must not call cudaMalloc (which can
+ * synchronise the device) or take a caching allocator's locks. The paper has
+ * no counterpart: this is an interface for such callers. Its scratch is a
+ * fixed device array inside the library, ckks_rescale_noalloc_capacity()
+ * bytes (32 MiB: a 2-polynomial tuple at N = 2^16 and level 32 fits
+ * exactly), held on every device that loads the library until exit; the call
+ * makes no cudaMalloc / cudaFree or other allocation. Inputs and outputs are
+ * still the caller's (in and out may be the same tuple). The first call on a
+ * device resolves the array's device address (once per device, with that
+ * device current); make that first call before any stream capture. The
+ * caller's current device is the same after the call as before it. Sizes
+ * whose scratch exceeds the capacity are rejected with CKKS_ENOMEM. All calls
+ * share the one array: calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and must be ordered by the
+ * caller. While the context's timing hook is on the call returns
+ * CKKS_EINVAL. */
 size_t ckks_rescale_noalloc_capacity(void);
 
 int ckks_rescale_multi_noalloc(ckks_context *ctx, const ckks_tuple *in, uint32_t mu, ckks_tuple *out, void *stream);
@@ -363,16 +368,40 @@ int ckks_counters(ckks_context *ctx, ckks_op_counters *out, int reset);
  * on the launch stream around every kernel the library enqueues (events
  * are created by the library on first use, never device memory).
  * ckks_profile_read waits for the recorded events and returns, per kernel
- * class, the launch count, the summed event time and the summed algorithmic
- * bytes (each input and output limb of a launch counted once). */
+ * class, the launch count, the summed event time, the summed algorithmic
+ * bytes (each input and output limb of a launch counted once) and the summed
+ * integer work: for the NTT / INTT phases the 64-bit Shoup products (one per
+ * butterfly, log2(n)/2 per element of an n-point phase, plus one per element
+ * for each fused scaling), for BConv and the key MAC the 64 x 64 -> 128-bit
+ * multiply-accumulates (Eq. 4 and Eq. 15 summed term by term); 0 for the
+ * other classes. */
 typedef struct {
     char name[24];
     uint64_t launches;
     double total_ms;
     double alg_bytes;
+    double int_ops;
 } ckks_kernel_stats;
 int ckks_profile_enable(ckks_context *ctx, int enable);
 int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, uint32_t *n_out);
+
+/* Integer-arithmetic peaks (measurement support; no counterpart in the
+ * paper). ckks_peak_int launches blocks x threads threads (threads a
+ * multiple of 32, at most 256) that each run ckks_peak_chains() independent
+ * chains of `iters` operations of one kind on registers only, and write one
+ * word per thread to `out` (device, blocks x threads words, caller-owned):
+ *   kind 0  lazy Shoup product x w - floor(x w' / 2^64) q (w' = floor(w 2^64 / q))
+ *   kind 1  lazy Cooley-Tukey butterfly of the NTT (Shoup product plus
+ *           Harvey's additions and correction)
+ *   kind 2  64 x 64 -> 128-bit multiply-accumulate
+ *   kind 3  Montgomery product, R = 2^64
+ * q: odd modulus below 2^62; w, wp: host arrays of ckks_peak_chains() Shoup
+ * pairs (w < q). The caller times the launch on `stream` with CUDA events:
+ * operations per second = blocks x threads x chains x iters / time.
+ * Returns CKKS_EINVAL for bad arguments, CKKS_ECUDA on a launch error. */
+int ckks_peak_chains(void);
+int ckks_peak_int(int kind, uint64_t q, const uint64_t *w, const uint64_t *wp, int blocks, int threads, int iters,
+                  uint64_t *out, void *stream);
 
 /* Launch tunables of a context; results are the same for every value.
  * Chosen by the autotuner: "ntt_tile_cols" / "ntt_tile_blocks" = elements

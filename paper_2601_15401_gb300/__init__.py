@@ -51,7 +51,7 @@ class _Request(ctypes.Structure):
 
 class _KStats(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
-                ("alg_bytes", ctypes.c_double)]
+                ("alg_bytes", ctypes.c_double), ("int_ops", ctypes.c_double)]
 
 
 class _Counters(ctypes.Structure):
@@ -491,7 +491,38 @@ class Context:
         n = ctypes.c_uint32()
         _check(lib().ckks_profile_read(self._h, arr, 16, ctypes.byref(n)), "ckks_profile_read")
         return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms,
-                                       "alg_bytes": arr[i].alg_bytes} for i in range(n.value)}
+                                       "alg_bytes": arr[i].alg_bytes, "int_ops": arr[i].int_ops}
+                for i in range(n.value)}
+
+
+PEAK_KINDS = {"shoup": 0, "butterfly": 1, "mac128": 2, "montgomery": 3}
+
+
+def peak_int(kind: str, q: int, blocks: int, threads: int = 256, iters: int = 4096, reps: int = 5,
+             stream=None) -> float:
+    """Measured rate (operations per second, best of `reps` CUDA-event timed
+    launches after one warm-up) of one integer operation of the hot path on
+    this GPU: "shoup", "butterfly", "mac128" or "montgomery" (ckks_peak_int)."""
+    import torch
+    chains = lib().ckks_peak_chains()
+    w = [(q - 1 - 977 * i) % q for i in range(chains)]
+    wp = [(x << 64) // q for x in w]
+    W = (ctypes.c_uint64 * chains)(*w)
+    WP = (ctypes.c_uint64 * chains)(*wp)
+    out = torch.empty(blocks * threads, dtype=torch.uint64, device="cuda")
+    st = torch.cuda.current_stream() if stream is None else stream
+    best = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(lib().ckks_peak_int(PEAK_KINDS[kind], q, W, WP, blocks, threads, iters, out.data_ptr(),
+                                   _stream(st)), "ckks_peak_int")
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        if r and (best is None or ms < best):
+            best = ms
+    return blocks * threads * chains * iters / (best / 1e3)
 
 
 def plan_optimize(k: int, criterion: str = "rs_units", level: int = 0, K: int = 0, alpha: int = 0):

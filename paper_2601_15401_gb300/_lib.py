@@ -81,6 +81,8 @@ SIGNATURES = {
     "ckks_tune_set": [V, ctypes.c_char_p, I],
     "ckks_tune_get": [V, ctypes.c_char_p, V],
     "ckks_strerror": [I],
+    "ckks_peak_chains": [],
+    "ckks_peak_int": [I, ctypes.c_uint64, V, V, I, I, I, V, V],
 }
 _VOID = {"ckks_context_destroy", "ckks_evk_set_destroy", "ckks_plan_destroy"}
 _STR = {"ckks_strerror"}

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.environ.get("CKKS_MULK_LIB", os.path.join(HERE, "libckks_mulk.so"))
-SOURCES = ["ntt.cu", "rns.cu", "context.cu", "engine.cu", "capi.cu", "plan.cpp", "noalloc.cu", "encrypt.cu", "galois.cu", "embed.cu", "check.cu"]
+SOURCES = ["ntt.cu", "rns.cu", "context.cu", "engine.cu", "capi.cu", "plan.cpp", "noalloc.cu", "encrypt.cu", "galois.cu", "embed.cu", "check.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -43,6 +43,20 @@ def _stale() -> bool:
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "ckks_mulk.h")]
     return any(os.path.getmtime(d) > t for d in deps)
+
+
+def source_hash() -> str:
+    """Hash of the library's sources (every file under csrc/ and the public
+    header): a tuning choice cached for one build is reused only while the
+    kernels it was measured and verified on are unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(os.listdir(CSRC))
+    for f in files:
+        h.update(f.encode())
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    h.update(open(os.path.join(HERE, "..", "include", "ckks_mulk.h"), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def build(force: bool = False, extra: list[str] | None = None, verbose: bool = False) -> str:

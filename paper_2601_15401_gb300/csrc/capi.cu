@@ -12,9 +12,6 @@
 
 using namespace ckks;
 
-struct ckks_context {
-    Context c;
-};
 struct ckks_evk_set {
     ckks_context *ctx;
     u64 *keys;
@@ -701,7 +698,7 @@ int ckks_profile_enable(ckks_context *ctx, int enable) {
 int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, uint32_t *n_out) {
     if (!ctx || !out || !n_out) return CKKS_EINVAL;
     cudaSetDevice(ctx->c.device);
-    double ms[KC_COUNT] = {0}, by[KC_COUNT] = {0};
+    double ms[KC_COUNT] = {0}, by[KC_COUNT] = {0}, ops[KC_COUNT] = {0};
     uint64_t cnt[KC_COUNT] = {0};
     for (const ProfRec &r : ctx->c.prof.recs) {
         if (cudaEventSynchronize(r.b) != cudaSuccess) return CKKS_ECUDA;
@@ -709,6 +706,7 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
         if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return CKKS_ECUDA;
         ms[r.cls] += t;
         by[r.cls] += r.bytes;
+        ops[r.cls] += r.ops;
         cnt[r.cls] += 1;
     }
     uint32_t n = 0;
@@ -719,6 +717,7 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
         out[n].launches = cnt[c];
         out[n].total_ms = ms[c];
         out[n].alg_bytes = by[c];
+        out[n].int_ops = ops[c];
         ++n;
     }
     *n_out = n;

@@ -291,8 +291,8 @@ void context_release(Context &C) {
 
 namespace ckks {
 
-ProfScope::ProfScope(const Context &c, int k, double by, cudaStream_t s)
-    : C(const_cast<Context *>(&c)), cls(k), bytes(by), st(s) {
+ProfScope::ProfScope(const Context &c, int k, double by, cudaStream_t s, double op)
+    : C(const_cast<Context *>(&c)), cls(k), bytes(by), ops(op), st(s) {
     Profiler &P = C->prof;
     if (!P.on) return;
     if (P.used + 2 > P.pool.size()) {
@@ -305,7 +305,7 @@ ProfScope::ProfScope(const Context &c, int k, double by, cudaStream_t s)
     cudaEvent_t a = P.pool[P.used++];
     b = P.pool[P.used++];
     cudaEventRecord(a, st);
-    P.recs.push_back(ProfRec{cls, a, b, bytes});
+    P.recs.push_back(ProfRec{cls, a, b, bytes, ops});
 }
 
 ProfScope::~ProfScope() {

@@ -18,9 +18,6 @@
 
 using namespace ckks;
 
-struct ckks_context {
-    Context c;
-};
 
 namespace {
 

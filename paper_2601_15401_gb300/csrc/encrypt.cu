@@ -17,9 +17,6 @@
 
 using namespace ckks;
 
-struct ckks_context {
-    Context c;
-};
 
 namespace {
 

@@ -594,6 +594,22 @@ size_t rescale_ws_bytes(const Context &C, int polys, int level, int mu, int B) {
     return ws.off;
 }
 
+// Algorithm 1 whatever the context's "inner_rescale" setting: the
+// allocation-free entry point sizes its fixed scratch for this form.
+size_t rescale_alg1_ws_bytes(const Context &C, int polys, int level, int mu, int B) {
+    Ws ws{nullptr, 0, 0, true};
+    LimbView v{};
+    multi_rs_alg1(C, ws, B, polys, level, mu, v, v, 0);
+    return ws.off;
+}
+
+int run_rescale_alg1_ws(const Context &C, int B, int polys, int level, int mu, LimbView in, LimbView out, void *wsp,
+                        size_t bytes, cudaStream_t st, cudaError_t &err) {
+    Ws ws{(char *)wsp, 0, bytes, false};
+    err = multi_rs_alg1(C, ws, B, polys, level, mu, in, out, st);
+    return err == cudaSuccess ? 0 : -5;
+}
+
 int run_rescale(const Context &C, int B, int polys, int level, int mu, LimbView in, LimbView out, Ws &ws,
                 cudaStream_t st, cudaError_t &err) {
     err = multi_rs(C, ws, B, polys, level, mu, in, out, st);

@@ -19,6 +19,9 @@ int run_relin_ws(const Context &C, int B, int n, int level, LimbView D, const u6
                  void *ws, size_t bytes, cudaStream_t st, cudaError_t &err);
 int run_rescale_ws(const Context &C, int B, int polys, int level, int mu, LimbView in, LimbView out, void *ws,
                    size_t bytes, cudaStream_t st, cudaError_t &err);
+size_t rescale_alg1_ws_bytes(const Context &C, int polys, int level, int mu, int B);
+int run_rescale_alg1_ws(const Context &C, int B, int polys, int level, int mu, LimbView in, LimbView out, void *ws,
+                        size_t bytes, cudaStream_t st, cudaError_t &err);
 int run_mul2_ws(const Context &C, int level, int B, LimbView a, LimbView b, LimbView out, const u64 *keys,
                 void *ws, size_t bytes, cudaStream_t st, cudaError_t &err);
 cudaError_t run_tensor(const Context &C, int B, int level, int m, const LimbView *in, const int *polys,

@@ -80,6 +80,7 @@ struct ProfRec {
     int cls;
     cudaEvent_t a, b;
     double bytes;
+    double ops;   // integer work units of the launch (see ProfScope)
 };
 
 struct Profiler {
@@ -140,14 +141,18 @@ struct Context {
 
 // Records CUDA events around one launch on its stream when the hook is on;
 // `bytes` is the launch's algorithmic traffic (each input and output limb
-// counted once).
+// counted once); `ops` its integer work: for NTT phases the Shoup products
+// (one per butterfly plus the fused load / store scalings), for BConv and
+// the key MAC the 64 x 64 -> 128-bit multiply-accumulates, 0 where not
+// counted.
 struct ProfScope {
     Context *C;
     int cls;
     double bytes;
+    double ops;
     cudaStream_t st;
     cudaEvent_t b = nullptr;
-    ProfScope(const Context &c, int k, double by, cudaStream_t s);
+    ProfScope(const Context &c, int k, double by, cudaStream_t s, double ops = 0.0);
     ~ProfScope();
 };
 
@@ -167,3 +172,9 @@ cudaError_t ntt_transform(const Context &C, bool fwd, const LimbJobs &J, const L
                           const StoreSpec *mid, cudaStream_t st);
 
 }  // namespace ckks
+
+// The opaque handle of the C ABI (include/ckks_mulk.h): one definition for
+// every translation unit that unwraps it.
+struct ckks_context {
+    ckks::Context c;
+};

@@ -449,8 +449,13 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
     if (S.mode == ST_MODDOWN) bytes += bp * S.K * limb;
     if (S.mode == ST_MRS) bytes += jobs_d * limb;
     if (S.mode == ST_ADDSUB) bytes += 2.0 * jobs_d * limb;
+    // integer work: one Shoup product per butterfly (log2 n stages of N / 2
+    // per limb) plus the Shoup products of the fused load / store
+    double ops = jobs_d * (double)C.N * 0.5 * logn;
+    if (L.mode == LD_EQ17) ops += jobs_d * (double)C.N * (L.mu + L.with_self);
+    if (S.mode == ST_SCALE || S.mode == ST_MODDOWN || S.mode == ST_MRS) ops += jobs_d * (double)C.N;
     ProfScope ps(C, fwd ? (cols ? KC_NTT_FWD_COLS : KC_NTT_FWD_BLOCKS) : (cols ? KC_NTT_INV_COLS : KC_NTT_INV_BLOCKS),
-                 bytes, st);
+                 bytes, st, ops);
     if (fwd) {
         return cols ? launch_phase_log<true, true>(logn, P, J, L, S, tiles, threads, smem, st)
                     : launch_phase_log<true, false>(logn, P, J, L, S, tiles, threads, smem, st);

@@ -178,7 +178,14 @@ cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) 
     count_op(C, OP_BCONV, (unsigned long long)A.n_t * A.n_digits * A.n_batch);
     // reads y' once, writes level + K - |digit| limbs per (t, digit)
     double limbs_out = (double)A.n_t * ((double)A.n_digits * (A.level + A.K) - A.level);
-    ProfScope ps(C, KC_BCONV, ((double)A.n_t * A.level + limbs_out) * A.n_batch * A.N * sizeof(u64), st);
+    // multiply-accumulates: per (t, digit) and coefficient, |digit| per target
+    double macs = 0;
+    for (int beta = 0; beta < A.n_digits; ++beta) {
+        const int na = std::min(A.level, (beta + 1) * A.alpha) - beta * A.alpha;
+        macs += (double)na * (A.level - na + A.K);
+    }
+    macs *= (double)A.n_t * A.n_batch * A.N;
+    ProfScope ps(C, KC_BCONV, ((double)A.n_t * A.level + limbs_out) * A.n_batch * A.N * sizeof(u64), st, macs);
     if (A.alpha <= 4) bconv_kernel<4><<<grid, thr, smem, st>>>(A);
     else if (A.alpha <= 8) bconv_kernel<8><<<grid, thr, smem, st>>>(A);
     else if (A.alpha <= 12) bconv_kernel<12><<<grid, thr, smem, st>>>(A);
@@ -243,7 +250,8 @@ cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
     const double terms = (double)(A.n - 1) * A.n_digits;
     const double limbs = (double)(A.level + A.K);
     double bytes = ((terms + 2.0) * A.n_batch + 2.0 * terms) * limbs * A.N * sizeof(u64);
-    ProfScope ps(C, KC_MAC, bytes, st);
+    const double macs = 2.0 * terms * limbs * A.n_batch * A.N;
+    ProfScope ps(C, KC_MAC, bytes, st, macs);
     mac_kernel<<<(unsigned)blocks, thr, 0, st>>>(A);
     return cudaGetLastError();
 }

@@ -172,6 +172,9 @@ TUNE_SPACE = {
     "bconv_threads": [128, 256, 512],
     "mac_threads": [128, 256, 512],
 }
+# the library's defaults (Context in csrc/internal.h): the reference every
+# candidate's output is compared with
+TUNE_DEFAULTS = {"ntt_tile_cols": 4096, "ntt_tile_blocks": 4096, "bconv_threads": 256, "mac_threads": 256}
 
 
 def _cache_path() -> str:
@@ -180,15 +183,24 @@ def _cache_path() -> str:
 
 
 def tune_key(ctx: Context) -> str:
+    """Cache key: GPU, parameter shape and the hash of the library sources, so
+    that a choice made for other kernels is never applied to these."""
+    from .build import source_hash
     name = torch.cuda.get_device_name(ctx.device).replace(" ", "_")
-    return f"{name}/logN{ctx.log_n}/L{ctx.L}/K{ctx.K}/dnum{ctx.dnum}"
+    return f"{name}/logN{ctx.log_n}/L{ctx.L}/K{ctx.K}/dnum{ctx.dnum}/src{source_hash()}"
 
 
 def autotune(ctx: Context, evk, k: int = 8, batch: int = 4, reps: int = 3, cache: str | None = None,
              force: bool = False) -> dict:
     """Pick each tunable by timing a batched k-input product (coordinate
     descent over TUNE_SPACE, CUDA events), store the choice in a JSON cache
-    keyed by GPU, N and the prime-chain shape, and apply it to `ctx`."""
+    keyed by GPU, N, the prime-chain shape and the library's source hash, and
+    apply it to `ctx`.
+
+    Every candidate's output is compared, residue for residue, with the
+    output of the library defaults on the same inputs; a candidate that
+    differs is rejected (never chosen), and a cached choice is re-checked the
+    same way before it is applied."""
     import synth
     path = cache or _cache_path()
     key = tune_key(ctx)
@@ -198,10 +210,6 @@ def autotune(ctx: Context, evk, k: int = 8, batch: int = 4, reps: int = 3, cache
             db = json.load(open(path))
         except Exception:
             db = {}
-    if key in db and not force:
-        for name, v in db[key]["choice"].items():
-            ctx.tune_set(name, v)
-        return db[key]
     level = ctx.L
     depth = ctx.plan_describe(k)["depth"]
     dev = torch.device("cuda", ctx.device)
@@ -211,9 +219,34 @@ def autotune(ctx: Context, evk, k: int = 8, batch: int = 4, reps: int = 3, cache
     outs = [Tuple(out[b], 2, level - depth, level - depth) for b in range(batch)]
     ws = torch.empty(ctx.workspace_size(k, level, batch) // 8 + 1, dtype=torch.uint64, device=dev)
 
-    def timed() -> float:
+    def apply(choice: dict):
+        for n, v in choice.items():
+            ctx.tune_set(n, v)
+
+    def run_once():
+        out.zero_()
         ctx.mul_k_batch(tup, evk, outs, ws)
         torch.cuda.synchronize(dev)
+        ctx.check()
+
+    apply(TUNE_DEFAULTS)
+    run_once()
+    reference = out.clone()
+
+    def same() -> bool:
+        return torch.equal(out.view(torch.int64), reference.view(torch.int64))
+
+    if key in db and not force:
+        apply(db[key]["choice"])
+        run_once()
+        if same():
+            return db[key]
+        apply(TUNE_DEFAULTS)  # a cached choice that no longer matches: search again
+
+    def timed() -> float:
+        run_once()
+        if not same():
+            return None
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
@@ -222,19 +255,30 @@ def autotune(ctx: Context, evk, k: int = 8, batch: int = 4, reps: int = 3, cache
         e1.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    choice = {n: ctx.tune_get(n) for n in TUNE_SPACE}
-    trials = {}
+    choice = dict(TUNE_DEFAULTS)
+    trials, rejected = {}, []
     for name, values in TUNE_SPACE.items():
         best = None
         for v in values:
             ctx.tune_set(name, v)
             ms = timed()
+            if ms is None:
+                rejected.append(f"{name}={v}")
+                continue
             trials[f"{name}={v}"] = round(ms, 4)
             if best is None or ms < best[0]:
                 best = (ms, v)
-        choice[name] = best[1]
-        ctx.tune_set(name, best[1])
-    entry = {"choice": choice, "ms": min(trials.values()), "trials": trials, "workload": f"k={k} batch={batch}"}
+        choice[name] = best[1] if best else TUNE_DEFAULTS[name]
+        ctx.tune_set(name, choice[name])
+    # the combination, checked once more as a whole
+    run_once()
+    if not same():
+        rejected.append("combined choice " + json.dumps(choice))
+        choice = dict(TUNE_DEFAULTS)
+        apply(choice)
+    entry = {"choice": choice, "ms": min(trials.values()), "trials": trials, "rejected": rejected,
+             "verified": "every candidate's output equal to the library defaults' output",
+             "workload": f"k={k} batch={batch}"}
     db[key] = entry
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -5,6 +5,13 @@ profiler captures (one kernel class at a time, a few GB on the device).
   python -m paper_2601_15401_gb300.microbench --op mul_k --k 8 --batch 4
   python -m paper_2601_15401_gb300.microbench --op rotate --batch 16
   python -m paper_2601_15401_gb300.microbench --op precision --batch 4 --secret-h 64
+  python -m paper_2601_15401_gb300.microbench --op peak
+
+--op peak measures the GPU's rate of each integer operation of the hot path
+(lazy Shoup product, lazy NTT butterfly, 64 x 64 -> 128-bit MAC, Montgomery
+product) with register-only kernels over a sweep of grid sizes, for a 50-bit
+and a 60-bit prime: the integer roofline the NTT / BConv / MAC fractions are
+taken against.
 
 --op precision prints, per k = 2..12, the largest slot error of the device
 round trip encode -> encrypt -> k-input product -> decrypt -> decode
@@ -26,7 +33,8 @@ def main():
     import synth
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "chain3", "rotate", "encode", "decode", "precision"], default="ntt")
+    ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "chain3", "rotate", "encode", "decode", "precision",
+                                         "peak"], default="ntt")
     ap.add_argument("--log-n", type=int, default=16)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--k", type=int, default=8)
@@ -47,6 +55,8 @@ def main():
     args = ap.parse_args()
     if args.op == "precision":
         return precision(args)
+    if args.op == "peak":
+        return peak(args)
     if args.params == "small":
         p = synth.params_small(log_n=args.log_n)
     elif args.params == "mid":
@@ -191,7 +201,27 @@ def main():
         "partition": args.partition, "graph": args.graph, "latency": latency,
         "ms_per_rep": round(e0.elapsed_time(e1) / args.reps, 4), "counters_per_rep": {n: v // args.reps for n, v in ctx.counters().items()},
         "kernels": {n: {"launches": v["launches"], "avg_us": round(v["total_ms"] * 1e3 / v["launches"], 2),
-                        "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1)} for n, v in prof.items()}}))
+                        "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1),
+                        "Gops": round(v["int_ops"] / (v["total_ms"] / 1e3) / 1e9, 2)} for n, v in prof.items()}}))
+
+
+def peak(args):
+    import torch
+
+    import paper_2601_15401_gb300 as G
+    import synth
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    res = {"op": "peak", "sms": sms, "gpu": torch.cuda.get_device_name(0), "unit": "G operations/s", "rates": {}}
+    for bits in (50, 60):
+        q = synth.prime_chain(bits, 1)[0]
+        for kind in G.PEAK_KINDS:
+            best = 0.0
+            for per_sm in (4, 8, 16):
+                r = G.peak_int(kind, q, blocks=sms * per_sm, threads=256, iters=2048)
+                best = max(best, r)
+                res["rates"][f"{kind}/{bits}bit/{per_sm}x256 per SM"] = round(r / 1e9, 2)
+            res["rates"][f"{kind}/{bits}bit/best"] = round(best / 1e9, 2)
+    print(json.dumps(res))
 
 
 def precision(args):
