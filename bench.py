@@ -372,7 +372,7 @@ def op_unit(kernel_class: str) -> str:
     """The integer operation a kernel class is built from (its roofline unit)."""
     if kernel_class.startswith("ntt"):
         return "butterfly"
-    if kernel_class in ("bconv", "mac"):
+    if kernel_class in ("bconv", "key_mac"):
         return "mac128"
     return ""
 

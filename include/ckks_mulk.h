@@ -289,6 +289,45 @@ int ckks_requests_workspace_size(const ckks_context *ctx, const ckks_request *re
 int ckks_mul_k_requests(ckks_context *ctx, const ckks_request *req, uint32_t n, uint32_t *done, void *workspace,
                         size_t ws_bytes, void *stream);
 
+/* Cross-shape batches ("waves", Section V's k-input products in any mix of
+ * k, partition and level, as one set of launches). A wave holds n products
+ * of one context: item i multiplies ct[0..k-1] (2 polynomials each, NTT
+ * form, one level) along `plan` into `out` (2 polynomials, level - depth),
+ * with the same residues as ckks_mul_k on that item alone. Inner tree nodes
+ * of all products are grouped by height and every stage (tensor product,
+ * Algorithm 1's transforms and rescale chain; at the roots ModUp, BConv,
+ * the key MAC of Eq. 15, ModDown of Eq. 11 / 12 and the relocated rescale)
+ * is one launch over every product with work there, its entries read from
+ * device tables. The paper's forms are always used (the "inner_rescale",
+ * "root_rescale", "moddown" and "check_residues" tunables do not apply).
+ *
+ * ckks_wave_create validates the items (as ckks_mul_k) and keeps their
+ * pointers (the wave borrows them: inputs and outputs must stay allocated
+ * while it is used); CKKS_EINVAL also for N <= 256 and for two items sharing
+ * one output. ckks_wave_workspace_size gives the bytes of the caller's
+ * device workspace (job tables, then every product's scratch).
+ * ckks_wave_run enqueues the wave on `stream` (256-byte aligned workspace);
+ * the first run with a given workspace writes the job tables into it with
+ * one host-to-device copy on the stream (later runs with the same workspace
+ * reuse them), so that first run should not be inside a stream capture.
+ * ckks_wave_describe returns the number of launches of a run and the number
+ * of inner-node heights (valid after the first run). ckks_wave_destroy
+ * waits for the wave's table copy, if one is in flight, and frees its host
+ * staging buffer. No device memory is allocated by the library. */
+typedef struct ckks_wave ckks_wave;
+typedef struct {
+    const ckks_tuple *ct;       /* k input ciphertexts */
+    uint32_t k;
+    const ckks_plan *plan;      /* partition tree for k inputs */
+    ckks_tuple *out;            /* output; level, scale and form are set by ckks_wave_run */
+} ckks_wave_item;
+int ckks_wave_create(ckks_context *ctx, const ckks_wave_item *items, uint32_t n, const ckks_evk_set *evk,
+                     ckks_wave **out);
+int ckks_wave_workspace_size(const ckks_wave *w, size_t *bytes);
+int ckks_wave_run(ckks_wave *w, void *workspace, size_t ws_bytes, void *stream);
+int ckks_wave_describe(const ckks_wave *w, uint32_t *n_launches, uint32_t *heights);
+void ckks_wave_destroy(ckks_wave *w);
+
 /* ckks_mul2: the standard 2-input multiply of Section II (Eq. 1-7): tensor
  * product, relinearisation with ModDown finished in the NTT domain, one RS in
  * the NTT domain (Eq. 7). The comparator for chained multiplication. Output

@@ -14,7 +14,7 @@ from dataclasses import dataclass
 
 from ._lib import ERRORS, CkksError, lib, library_path
 
-__all__ = ["Context", "Tuple", "CkksError", "library_path", "lib", "TABLE_II", "plan_optimize"]
+__all__ = ["Context", "Tuple", "Wave", "CkksError", "library_path", "lib", "TABLE_II", "plan_optimize"]
 
 TABLE_II = {
     2: "(1,1)", 3: "(1,1,1)", 4: "(2,2)", 5: "(2,2,1)", 6: "(3,3)", 7: "(4,3)|(2,2)",
@@ -47,6 +47,10 @@ class _Tuple(ctypes.Structure):
 class _Request(ctypes.Structure):
     _fields_ = [("ct", ctypes.c_void_p), ("k", ctypes.c_uint32), ("batch", ctypes.c_uint32),
                 ("evk", ctypes.c_void_p), ("plan", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class _WaveItem(ctypes.Structure):
+    _fields_ = [("ct", ctypes.c_void_p), ("k", ctypes.c_uint32), ("plan", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 
 class _KStats(ctypes.Structure):
@@ -493,6 +497,59 @@ class Context:
         return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms,
                                        "alg_bytes": arr[i].alg_bytes, "int_ops": arr[i].int_ops}
                 for i in range(n.value)}
+
+
+class Wave:
+    """A cross-shape batch of k-input products of one context (ckks_wave_*):
+    items = [(inputs: list of k Tuples, out: Tuple, partition or None)], any
+    mix of k, partitions and levels. Every stage of every product runs in one
+    launch per stage (job tables on the device); results equal ckks_mul_k on
+    each item alone. The wave borrows the tuples' device memory."""
+
+    def __init__(self, ctx: "Context", items, evk):
+        self.ctx = ctx
+        self._keep = []
+        arr = (_WaveItem * len(items))()
+        self.outs = []
+        for i, (cts, out, part) in enumerate(items):
+            k = len(cts)
+            ct = (_Tuple * k)(*[c.c() for c in cts])
+            o = out.c()
+            self._keep += [ct, o]
+            arr[i] = _WaveItem(ctypes.cast(ct, ctypes.c_void_p), k, ctx.plan(k, part), ctypes.addressof(o))
+            self.outs.append((out, o))
+        self._keep.append(arr)
+        h = ctypes.c_void_p()
+        _check(lib().ckks_wave_create(ctx._h, arr, len(items), evk._h, ctypes.byref(h)), "ckks_wave_create")
+        self._h = h
+
+    def workspace_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ckks_wave_workspace_size(self._h, ctypes.byref(n)), "ckks_wave_workspace_size")
+        return n.value
+
+    def run(self, workspace, stream=None):
+        _check(lib().ckks_wave_run(self._h, workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                   _stream(stream)), "ckks_wave_run")
+        for out, o in self.outs:
+            out.level, out.n_polys, out.ntt_form, out.scale, out.poly_stride = (o.level, o.n_polys, o.ntt_form,
+                                                                                o.scale, o.poly_stride)
+
+    def describe(self) -> dict:
+        n, h = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().ckks_wave_describe(self._h, ctypes.byref(n), ctypes.byref(h)), "ckks_wave_describe")
+        return {"launches": n.value, "heights": h.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ckks_wave_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 PEAK_KINDS = {"shoup": 0, "butterfly": 1, "mac128": 2, "montgomery": 3}

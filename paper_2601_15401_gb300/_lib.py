@@ -82,9 +82,14 @@ SIGNATURES = {
     "ckks_tune_get": [V, ctypes.c_char_p, V],
     "ckks_strerror": [I],
     "ckks_peak_chains": [],
+    "ckks_wave_create": [V, V, U32, V, V],
+    "ckks_wave_workspace_size": [V, V],
+    "ckks_wave_run": [V, V, SZ, V],
+    "ckks_wave_describe": [V, V, V],
+    "ckks_wave_destroy": [V],
     "ckks_peak_int": [I, ctypes.c_uint64, V, V, I, I, I, V, V],
 }
-_VOID = {"ckks_context_destroy", "ckks_evk_set_destroy", "ckks_plan_destroy"}
+_VOID = {"ckks_context_destroy", "ckks_evk_set_destroy", "ckks_plan_destroy", "ckks_wave_destroy"}
 _STR = {"ckks_strerror"}
 _SIZE = {"ckks_rescale_noalloc_capacity"}
 

@@ -12,12 +12,6 @@
 
 using namespace ckks;
 
-struct ckks_evk_set {
-    ckks_context *ctx;
-    u64 *keys;
-    uint32_t t_max;
-    unsigned long long sum;  // checksum of the prepared keys, taken at creation
-};
 
 static long long evk_words(const Context &C, uint32_t t_max) {
     return (long long)(t_max - 1) * C.dnum * 2 * (C.L + C.K) * C.N;
@@ -40,9 +34,6 @@ static cudaError_t take_residue_count(const Context &C, cudaStream_t st, unsigne
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
 }
-struct ckks_plan {
-    Plan p;
-};
 
 static int cuda_fail(ckks_context *ctx, cudaError_t e) {
     if (e != cudaSuccess) {
@@ -249,18 +240,6 @@ int ckks_workspace_size(const ckks_context *ctx, const ckks_plan *plan, uint32_t
 }
 
 // scale of the result: product of input scales / primes divided at each node
-static double plan_scale(const Context &C, const Plan &P, int level, const double *scales) {
-    std::vector<int> lin, lout, polys;
-    plan_levels(P, level, lin, lout, polys);
-    std::vector<double> sc(P.nodes.size(), 1.0);
-    for (size_t i = 0; i < P.nodes.size(); ++i) {
-        double s = 1.0;
-        for (int c : P.nodes[i].children) s *= c >= 0 ? sc[c] : scales[-1 - c];
-        for (int j = 0; j < P.nodes[i].mu; ++j) s /= (double)C.primes[lin[i] - 1 - j];
-        sc[i] = s;
-    }
-    return sc.back();
-}
 
 static int mul_k_common(ckks_context *ctx, const ckks_tuple *ct, uint32_t k, uint32_t batch, const ckks_evk_set *evk,
                         const ckks_plan *plan, ckks_tuple *out, void *ws, size_t ws_bytes, void *stream) {

@@ -524,6 +524,21 @@ int run_mul_k(const Context &C, const Plan &P, int level, int B, const LimbView 
     return 0;
 }
 
+// Output scale of a plan: the product of the children's scales at every
+// node, divided by each prime a rescale removes.
+double plan_scale(const Context &C, const Plan &P, int level, const double *scales) {
+    std::vector<int> lin, lout, polys;
+    plan_levels(P, level, lin, lout, polys);
+    std::vector<double> sc(P.nodes.size(), 1.0);
+    for (size_t i = 0; i < P.nodes.size(); ++i) {
+        double s = 1.0;
+        for (int c : P.nodes[i].children) s *= c >= 0 ? sc[c] : scales[-1 - c];
+        for (int j = 0; j < P.nodes[i].mu; ++j) s /= (double)C.primes[lin[i] - 1 - j];
+        sc[i] = s;
+    }
+    return sc.back();
+}
+
 size_t relin_ws_bytes(const Context &C, int n, int level, int B) {
     Ws ws{nullptr, 0, 0, true};
     LimbView d{};

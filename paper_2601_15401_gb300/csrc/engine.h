@@ -29,6 +29,10 @@ cudaError_t run_tensor(const Context &C, int B, int level, int m, const LimbView
 cudaError_t transform_plain(const Context &C, bool fwd, int B, int polys, int level, LimbView in, LimbView out,
                             cudaStream_t st);
 
+// scale of a plan's output from the inputs' scales (Section V: each
+// rescale divides by the prime it removes)
+double plan_scale(const Context &C, const Plan &P, int level, const double *scales);
+
 int context_build(Context &C, uint32_t log_n, uint32_t L, uint32_t K, uint32_t dnum, const u64 *q, const u64 *p,
                   int device);
 void context_release(Context &C);

@@ -61,6 +61,24 @@ struct StoreSpec {
     int K;
 };
 
+// One limb of an NTT phase launch whose limbs come from a device table
+// (cross-shape launches): every pointer is the limb's own; the load and
+// store modes and the per-prime constant tables stay per launch (LoadSpec /
+// StoreSpec).
+struct NttJob {
+    const u64 *a;       // load: input limb (LD_PLAIN, first addend of LD_ADD, self term of LD_EQ17)
+    const u64 *b;       // load: LD_ADD second addend; LD_EQ17 / LD_BCONVK first of the limbs N apart
+    u64 *dst;           // store: output limb
+    const u64 *aux;     // store: ST_MRS A limb; ST_MODDOWN first z limb (limbs N apart); ST_ADDSUB first addend
+    const u64 *aux2;    // store: ST_ADDSUB second addend
+    const Shoup *g;     // LD_EQ17: g[0..mu-1], g[mu] = self
+    const Shoup *c;     // ST_SCALE / ST_MODDOWN / ST_MRS constant
+    int prime;          // prime index (Q primes first, then P primes)
+    int mu;             // LD_EQ17
+    int with_self;      // LD_EQ17
+    int pad;
+};
+
 // Kernel classes of the timing hook.
 enum KernelClass {
     KC_NTT_FWD_COLS = 0,
@@ -166,6 +184,11 @@ inline void count_kernel(const Context &C) { count_op(C, OP_KERNELS, 1); }
 
 // ntt.cu
 void ntt_geometry(int logN, int &log_n1, int &log_n2);
+// phase launch over a device table of NttJob (ntt_launch.cu); jobs: device
+// array of n_jobs entries
+cudaError_t launch_ntt_phase_table(const Context &C, bool fwd, bool cols, const NttJob *jobs, int n_jobs,
+                                   const LoadSpec &L, const StoreSpec &S, double alg_bytes, double ops,
+                                   cudaStream_t st);
 cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJobs &J, const LoadSpec &L,
                              const StoreSpec &S, cudaStream_t st);
 cudaError_t ntt_transform(const Context &C, bool fwd, const LimbJobs &J, const LoadSpec &L, const StoreSpec &S,
@@ -177,4 +200,12 @@ cudaError_t ntt_transform(const Context &C, bool fwd, const LimbJobs &J, const L
 // every translation unit that unwraps it.
 struct ckks_context {
     ckks::Context c;
+};
+
+// The evaluation-key set and the plan handles of the C ABI.
+struct ckks_evk_set {
+    ckks_context *ctx;
+    u64 *keys;
+    uint32_t t_max;
+    unsigned long long sum;  // checksum of the prepared keys, taken at creation
 };

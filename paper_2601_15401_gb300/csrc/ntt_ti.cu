@@ -1,0 +1,13 @@
+// Instantiations of the inverse table-driven (cross-shape) NTT phase kernels (ntt_kernel.cuh);
+// one translation unit per direction and job source so that they compile in
+// parallel.
+#include "ntt_kernel.cuh"
+
+namespace ckks {
+
+cudaError_t ntt_dispatch_table_inv(bool cols, int logn, const NttPhase &P, const NttJob *jobs, int n_jobs,
+                                  const LoadSpec &L, const StoreSpec &S, const PhaseLaunch &G) {
+    return dispatch_phase<false, true>(cols, logn, P, nullptr, jobs, n_jobs, L, S, G);
+}
+
+}  // namespace ckks

@@ -33,3 +33,8 @@ double plan_cost(const Plan &P, int criterion, int level, int K, int alpha);
 int plan_optimize(int k, int criterion, int level, int K, int alpha, std::string &best_text, double &best_cost);
 
 }  // namespace ckks
+
+// The plan handle of the C ABI.
+struct ckks_plan {
+    ckks::Plan p;
+};

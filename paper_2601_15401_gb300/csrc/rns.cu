@@ -24,29 +24,50 @@ static constexpr int kThreads = 256;
 // wise in the NTT domain. Each child product is a Montgomery product, so the
 // result carries R^-(m-1); the final multiply by R^m (REDC) removes it.
 // ---------------------------------------------------------------------------
+// Where a tensor-product CTA finds its children and output: the uniform
+// batch of a launch (TensorArgs, batch element b) or one table entry.
+struct TensorUniformView {
+    const TensorArgs &A;
+    int b;
+    __device__ __forceinline__ int m() const { return A.m; }
+    __device__ __forceinline__ int polys(int c) const { return A.child_polys[c]; }
+    __device__ __forceinline__ const u64 *src(int c) const { return A.child[c].ptr + (i64)b * A.child[c].bstride; }
+    __device__ __forceinline__ i64 pstride(int c) const { return A.child[c].pstride; }
+    __device__ __forceinline__ u64 *dst() const { return A.out.ptr + (i64)b * A.out.bstride; }
+    __device__ __forceinline__ i64 dstride() const { return A.out.pstride; }
+};
+
+struct TensorTableView {
+    const TensorJob &J;
+    __device__ __forceinline__ int m() const { return J.m; }
+    __device__ __forceinline__ int polys(int c) const { return J.cpolys[c]; }
+    __device__ __forceinline__ const u64 *src(int c) const { return J.child[c]; }
+    __device__ __forceinline__ i64 pstride(int c) const { return J.cstride[c]; }
+    __device__ __forceinline__ u64 *dst() const { return J.out; }
+    __device__ __forceinline__ i64 dstride() const { return J.ostride; }
+};
+
 // MAXT bounds every tuple size involved (children and output), so the
 // unrolled, predicated product loops stay short for small nodes.
-template <int MAXT>
-__global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
-    const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;  // limb * N + coefficient
-    if (r >= (i64)A.level * A.N) return;
-    const int b = blockIdx.y;
-    const int j = (int)(r >> A.log_n);
-    const ModQ m = A.mods[j];
+// r = limb * N + coefficient, j = the limb's prime.
+template <int MAXT, class V>
+__device__ __forceinline__ void tensor_coeff(const V &v, i64 r, int j, const ModQ m, const u64 *rpow) {
     const u64 q = m.q;
     u64 cur[MAXT];
-    int ncur = A.child_polys[0];
+    int ncur = v.polys(0);
     {
-        const u64 *src = A.child[0].ptr + (i64)b * A.child[0].bstride + r;
+        const u64 *src = v.src(0) + r;
+        const i64 ps = v.pstride(0);
 #pragma unroll
-        for (int a = 0; a < MAXT; ++a) cur[a] = a < ncur ? src[(i64)a * A.child[0].pstride] : 0ull;
+        for (int a = 0; a < MAXT; ++a) cur[a] = a < ncur ? src[(i64)a * ps] : 0ull;
     }
-    for (int c = 1; c < A.m; ++c) {
-        const int ny = A.child_polys[c];
-        const u64 *src = A.child[c].ptr + (i64)b * A.child[c].bstride + r;
+    for (int c = 1; c < v.m(); ++c) {
+        const int ny = v.polys(c);
+        const u64 *src = v.src(c) + r;
+        const i64 ps = v.pstride(c);
         u64 y[MAXT];
 #pragma unroll
-        for (int a = 0; a < MAXT; ++a) y[a] = a < ny ? src[(i64)a * A.child[c].pstride] : 0ull;
+        for (int a = 0; a < MAXT; ++a) y[a] = a < ny ? src[(i64)a * ps] : 0ull;
         u64 nxt[MAXT];
         if (ny == 2) {
             // times a ciphertext (y0 + y1 s): Karatsuba on pairs of the running
@@ -93,11 +114,34 @@ __global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
 #pragma unroll
         for (int t = 0; t < MAXT; ++t) cur[t] = nxt[t];
     }
-    const u64 fix = A.rpow[(i64)j * 16 + A.m];  // R^m
-    u64 *dst = A.out.ptr + (i64)b * A.out.bstride + r;
+    const u64 fix = rpow[(i64)j * 16 + v.m()];  // R^m
+    u64 *dst = v.dst() + r;
+    const i64 ds = v.dstride();
 #pragma unroll
     for (int t = 0; t < MAXT; ++t)
-        if (t < ncur) dst[(i64)t * A.out.pstride] = mont_mul(cur[t], fix, m);
+        if (t < ncur) dst[(i64)t * ds] = mont_mul(cur[t], fix, m);
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
+    const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;  // limb * N + coefficient
+    if (r >= (i64)A.level * A.N) return;
+    const int j = (int)(r >> A.log_n);
+    tensor_coeff<MAXT>(TensorUniformView{A, (int)blockIdx.y}, r, j, A.mods[j], A.rpow);
+}
+
+// Table launch: blockIdx.y = tree node; the node's entry is staged in shared
+// memory (it is indexed by child at run time).
+template <int MAXT>
+__global__ void __launch_bounds__(kThreads) tensor_table_kernel(const TensorJob *jobs, int N, int log_n,
+                                                                const ModQ *mods, const u64 *rpow) {
+    __shared__ TensorJob J;
+    if (threadIdx.x == 0) J = jobs[blockIdx.y];
+    __syncthreads();
+    const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (i64)J.level * N) return;
+    const int j = (int)(r >> log_n);
+    tensor_coeff<MAXT>(TensorTableView{J}, r, j, mods[j], rpow);
 }
 
 cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t st) {
@@ -122,12 +166,68 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_jobs, int maxt, int max_level,
+                                double bytes, cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    if (n_jobs > 65535) return cudaErrorInvalidValue;
+    dim3 blocks((unsigned)(((i64)max_level * C.N + kThreads - 1) / kThreads), (unsigned)n_jobs);
+    count_kernel(C);
+    ProfScope ps(C, KC_TENSOR, bytes, st);
+    if (maxt <= 3) tensor_table_kernel<3><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else if (maxt <= 4) tensor_table_kernel<4><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else if (maxt <= 5) tensor_table_kernel<5><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else if (maxt <= 7) tensor_table_kernel<7><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else if (maxt <= 9) tensor_table_kernel<9><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else tensor_table_kernel<CKKS_MAX_TUPLE><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // ModUp basis conversion (Eq. 4), coefficient domain:
 //   ext[x] = sum_{j in digit} y'_j [(Q_beta / q_j) mod x]   (mod x)
 // y'_j = [y_j (Q_beta/q_j)^-1]_{q_j} was produced by the INTT's epilogue.
 // blockIdx.y = (t, beta) job, blockIdx.z = batch.
 // ---------------------------------------------------------------------------
+// One CTA: the constants of (level, digit) staged in shared memory, then one
+// coefficient per thread. y: limb 0 of the prescaled d_t; dst: slot 0 of the
+// (t, digit) ModUp output.
+template <int AMAX>
+__device__ __forceinline__ void bconv_block(const u64 *ctab, const u64 *y0, u64 *dst0, int level, int beta,
+                                            int alpha, int L, int K, int n_primes, int N, const ModQ *mods, u64 *cs) {
+    const int d0 = beta * alpha;
+    int d1 = d0 + alpha;
+    if (d1 > level) d1 = level;
+    const int na = d1 - d0;
+    // targets: Q limbs outside the digit, then every P limb
+    const int nq_t = level - na;
+    const int n_t = nq_t + K;
+    for (int i = threadIdx.x; i < na * n_t; i += blockDim.x) {
+        int jj = i / n_t, ti = i % n_t;
+        int x = ti < nq_t ? (ti < d0 ? ti : ti + na) : L + (ti - nq_t);
+        cs[i] = ctab[(i64)jj * n_primes + x];
+    }
+    __syncthreads();
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const u64 *ysrc = y0 + e;
+    u64 y[AMAX];
+#pragma unroll
+    for (int jj = 0; jj < AMAX; ++jj) y[jj] = jj < na ? ysrc[(i64)(d0 + jj) * N] : 0ull;
+    u64 *dst = dst0 + e;
+    for (int ti = 0; ti < n_t; ++ti) {
+        const int slot = ti < nq_t ? (ti < d0 ? ti : ti + na) : level + (ti - nq_t);
+        const int x = ti < nq_t ? slot : L + (ti - nq_t);
+        const ModQ m = mods[x];
+        // sum over the digit: hi stays below q because the digit's primes sum to < 2^64
+        Acc128Lazy acc;
+        acc.zero();
+#pragma unroll
+        for (int jj = 0; jj < AMAX; ++jj)
+            if (jj < na) acc.mac(y[jj], cs[jj * n_t + ti]);
+        dst[(i64)slot * N] = redc(acc.hi, acc.lo, m);
+    }
+}
+
 template <int AMAX>
 __global__ void __launch_bounds__(1024) bconv_kernel(BconvArgs A) {
     extern __shared__ u64 cs[];  // [alpha][n_targets] Montgomery constants
@@ -135,39 +235,19 @@ __global__ void __launch_bounds__(1024) bconv_kernel(BconvArgs A) {
     const int b = blockIdx.z;
     const int t = job / A.n_digits;
     const int beta = job % A.n_digits;
-    const int d0 = beta * A.alpha;
-    int d1 = d0 + A.alpha;
-    if (d1 > A.level) d1 = A.level;
-    const int na = d1 - d0;
-    // targets: Q limbs outside the digit, then every P limb
-    const int nq_t = A.level - na;
-    const int n_t = nq_t + A.K;
-    const u64 *ctab = A.consts + (i64)beta * A.alpha * A.n_primes;
-    for (int i = threadIdx.x; i < na * n_t; i += blockDim.x) {
-        int jj = i / n_t, ti = i % n_t;
-        int x = ti < nq_t ? (ti < d0 ? ti : ti + na) : A.L + (ti - nq_t);
-        cs[i] = ctab[(i64)jj * A.n_primes + x];
-    }
-    __syncthreads();
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= A.N) return;
-    const u64 *ysrc = A.y.ptr + (i64)b * A.y.bstride + (i64)t * A.y.pstride + e;
-    u64 y[AMAX];
-#pragma unroll
-    for (int jj = 0; jj < AMAX; ++jj) y[jj] = jj < na ? ysrc[(i64)(d0 + jj) * A.N] : 0ull;
-    u64 *dst = A.ext.ptr + (i64)b * A.ext.bstride + (i64)(t * A.n_digits + beta) * A.ext.pstride + e;
-    for (int ti = 0; ti < n_t; ++ti) {
-        const int slot = ti < nq_t ? (ti < d0 ? ti : ti + na) : A.level + (ti - nq_t);
-        const int x = ti < nq_t ? slot : A.L + (ti - nq_t);
-        const ModQ m = A.mods[x];
-        // sum over the digit: hi stays below q because the digit's primes sum to < 2^64
-        Acc128Lazy acc;
-        acc.zero();
-#pragma unroll
-        for (int jj = 0; jj < AMAX; ++jj)
-            if (jj < na) acc.mac(y[jj], cs[jj * n_t + ti]);
-        dst[(i64)slot * A.N] = redc(acc.hi, acc.lo, m);
-    }
+    bconv_block<AMAX>(A.consts + (i64)beta * A.alpha * A.n_primes,
+                      A.y.ptr + (i64)b * A.y.bstride + (i64)t * A.y.pstride,
+                      A.ext.ptr + (i64)b * A.ext.bstride + (i64)(t * A.n_digits + beta) * A.ext.pstride, A.level, beta,
+                      A.alpha, A.L, A.K, A.n_primes, A.N, A.mods, cs);
+}
+
+// Table launch: blockIdx.y = (product, d_t, digit) entry.
+template <int AMAX>
+__global__ void __launch_bounds__(1024) bconv_table_kernel(const BconvJob *jobs, int alpha, int L, int K,
+                                                           int n_primes, int N, const ModQ *mods) {
+    extern __shared__ u64 cs[];
+    const BconvJob J = jobs[blockIdx.y];
+    bconv_block<AMAX>(J.consts, J.y, J.ext, J.level, J.beta, alpha, L, K, n_primes, N, mods, cs);
 }
 
 cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) {
@@ -190,6 +270,24 @@ cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) 
     else if (A.alpha <= 8) bconv_kernel<8><<<grid, thr, smem, st>>>(A);
     else if (A.alpha <= 12) bconv_kernel<12><<<grid, thr, smem, st>>>(A);
     else bconv_kernel<16><<<grid, thr, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_jobs, double bytes, double macs,
+                               cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    if (n_jobs > 65535) return cudaErrorInvalidValue;
+    const int thr = C.tune_bconv_threads;
+    dim3 grid((C.N + thr - 1) / thr, (unsigned)n_jobs);
+    size_t smem = (size_t)C.alpha * (C.L + C.K) * sizeof(u64);
+    count_kernel(C);
+    count_op(C, OP_BCONV, (unsigned long long)n_jobs);
+    ProfScope ps(C, KC_BCONV, bytes, st, macs);
+    const int np = C.L + C.K;
+    if (C.alpha <= 4) bconv_table_kernel<4><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else if (C.alpha <= 8) bconv_table_kernel<8><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else if (C.alpha <= 12) bconv_table_kernel<12><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else bconv_table_kernel<16><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
     return cudaGetLastError();
 }
 
@@ -256,12 +354,81 @@ cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Table launch of the key MAC: blockIdx.x = accumulator limb (product, x),
+// ordered by prime so that neighbouring blocks read the same key rows;
+// blockIdx.y = coefficient chunk.
+__global__ void __launch_bounds__(1024) mac_table_kernel(const MacJob *jobs, const MacTarget *targets, const u64 *keys,
+                                                         i64 key_pstride, int key_digits, int alpha, int L, int N,
+                                                         const ModQ *mods) {
+    const MacTarget T = targets[blockIdx.x];
+    const MacJob J = jobs[T.job];
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int x = T.x;
+    const bool isq = x < J.level;
+    const int prime = isq ? x : L + (x - J.level);
+    const ModQ m = mods[prime];
+    const u64 q = m.q;
+    const int my_digit = isq ? x / alpha : -1;
+    Acc128 acc0, acc1;
+    acc0.zero();
+    acc1.zero();
+    const i64 key_row = (i64)prime * N + e;
+    const i64 off = (i64)x * N + e;
+    for (int t = 2; t <= J.n; ++t) {
+        for (int beta = 0; beta < J.nd; ++beta) {
+            const u64 term = beta == my_digit ? J.d[(i64)t * J.dstride + off]
+                                              : J.ext[(i64)((t - 2) * J.nd + beta) * J.estride + off];
+            const u64 *key = keys + ((i64)((t - 2) * key_digits + beta) * 2) * key_pstride;
+            acc0.mac(term, key[key_row], q);
+            acc1.mac(term, key[key_pstride + key_row], q);
+        }
+    }
+    u64 *dst = J.acc + off;
+    dst[0] = redc(acc0.hi, acc0.lo, m);
+    dst[J.astride] = redc(acc1.hi, acc1.lo, m);
+}
+
+cudaError_t launch_mac_table(const Context &C, const MacJob *jobs, const MacTarget *targets, int n_targets,
+                             const u64 *keys, double bytes, double macs, cudaStream_t st) {
+    if (n_targets <= 0) return cudaSuccess;
+    const int thr = C.tune_mac_threads;
+    const int chunks = (C.N + thr - 1) / thr;
+    if (chunks > 65535) return cudaErrorInvalidValue;
+    count_kernel(C);
+    ProfScope ps(C, KC_MAC, bytes, st, macs);
+    dim3 grid((unsigned)n_targets, (unsigned)chunks);
+    mac_table_kernel<<<grid, thr, 0, st>>>(jobs, targets, keys, (i64)(C.L + C.K) * C.N, C.dnum, C.alpha, C.L, C.N,
+                                           C.d_mods);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Rescale chain among the mu top limbs (coefficient domain), in place:
 // a^{(t),{u}} = q_{l-u}^-1 (a^{(t),{u-1}} - a^{(l-u),{u-1}}) mod q_t for
 // u = 1..mu-1 and t < l-u (Eq. 6 applied inside Algorithm 1, step 2).
 // After it, limb t holds a^{(t),{l-1-t}}.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void rschain_coeff(u64 *base, int N, int level, int mu, const ModQ *mods, const Shoup *one,
+                                              const Shoup *invq) {
+    const int l0 = level - mu;
+    u64 a[CKKS_MAX_PRIMES];
+    for (int t = 0; t < mu; ++t) a[t] = base[(i64)t * N];
+    for (int u = 1; u < mu; ++u) {
+        const int top = mu - u;  // index of limb level-u
+        const int ptop = l0 + top;
+        for (int t = 0; t < top; ++t) {
+            const int pt = l0 + t;
+            const u64 qt = mods[pt].q;
+            const Shoup o = one[pt];
+            const u64 tr = shoup(a[top], o.w, o.wp, qt);  // a[top] mod q_t
+            const Shoup inv = invq[ptop * CKKS_MAX_PRIMES + pt];
+            a[t] = shoup(sub_mod(a[t], tr, qt), inv.w, inv.wp, qt);
+        }
+    }
+    for (int t = 0; t < mu - 1; ++t) base[(i64)t * N] = a[t];
+}
+
 __global__ void __launch_bounds__(kThreads) rschain_kernel(RsChainArgs A) {
     const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const i64 per = (i64)A.n_polys * A.N;
@@ -270,22 +437,18 @@ __global__ void __launch_bounds__(kThreads) rschain_kernel(RsChainArgs A) {
     const int p = (int)((gid % per) / A.N);
     const int e = (int)(gid % A.N);
     u64 *base = A.v.ptr + (i64)b * A.v.bstride + (i64)p * A.v.pstride + e;  // slot 0 = limb level - mu
-    const int l0 = A.level - A.mu;
-    u64 a[CKKS_MAX_PRIMES];
-    for (int t = 0; t < A.mu; ++t) a[t] = base[(i64)t * A.N];
-    for (int u = 1; u < A.mu; ++u) {
-        const int top = A.mu - u;  // index of limb level-u
-        const int ptop = l0 + top;
-        for (int t = 0; t < top; ++t) {
-            const int pt = l0 + t;
-            const u64 qt = A.mods[pt].q;
-            const Shoup one = A.one[pt];
-            const u64 tr = shoup(a[top], one.w, one.wp, qt);  // a[top] mod q_t
-            const Shoup inv = A.invq[ptop * CKKS_MAX_PRIMES + pt];
-            a[t] = shoup(sub_mod(a[t], tr, qt), inv.w, inv.wp, qt);
-        }
-    }
-    for (int t = 0; t < A.mu - 1; ++t) base[(i64)t * A.N] = a[t];
+    rschain_coeff(base, A.N, A.level, A.mu, A.mods, A.one, A.invq);
+}
+
+// Table launch: blockIdx.y = tuple entry, x over its polynomials x coefficients.
+__global__ void __launch_bounds__(kThreads) rschain_table_kernel(const RsJob *jobs, int N, const ModQ *mods,
+                                                                 const Shoup *one, const Shoup *invq) {
+    const RsJob J = jobs[blockIdx.y];
+    const i64 gid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (i64)J.n_polys * N) return;
+    const int p = (int)(gid / N);
+    const int e = (int)(gid % N);
+    rschain_coeff(J.v + (i64)p * J.pstride + e, N, J.level, J.mu, mods, one, invq);
 }
 
 cudaError_t launch_rschain(const Context &C, const RsChainArgs &A, cudaStream_t st) {
@@ -294,6 +457,17 @@ cudaError_t launch_rschain(const Context &C, const RsChainArgs &A, cudaStream_t 
     count_kernel(C);
     ProfScope ps(C, KC_RSCHAIN, 2.0 * A.n_batch * A.n_polys * A.mu * A.N * sizeof(u64), st);
     rschain_kernel<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rschain_table(const Context &C, const RsJob *jobs, int n_jobs, int max_polys, double bytes,
+                                 cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    if (n_jobs > 65535) return cudaErrorInvalidValue;
+    count_kernel(C);
+    ProfScope ps(C, KC_RSCHAIN, bytes, st);
+    dim3 grid((unsigned)(((i64)max_polys * C.N + kThreads - 1) / kThreads), (unsigned)n_jobs);
+    rschain_table_kernel<<<grid, kThreads, 0, st>>>(jobs, C.N, C.d_mods, C.d_one, C.d_invq);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,53 @@ struct AutoMap {
     int src[16];
 };
 
+// Cross-shape launches: entries of different products, levels and tree
+// nodes of one context in one launch, read from device tables.
+struct TensorJob {                       // one tree node of one product
+    const u64 *child[CKKS_MAX_CHILDREN]; // limb 0 of polynomial 0 of each child
+    i64 cstride[CKKS_MAX_CHILDREN];      // polynomial stride of each child (elements)
+    int cpolys[CKKS_MAX_CHILDREN];
+    u64 *out;                            // limb 0 of polynomial 0 of the product tuple
+    i64 ostride;
+    int m, level;
+};
+
+struct RsJob {                           // the mu top limbs of every polynomial of one tuple
+    u64 *v;                              // limb level - mu of polynomial 0
+    i64 pstride;
+    int n_polys, level, mu, pad;
+};
+
+struct BconvJob {                        // one (d_t, digit) of one product
+    const u64 *y;                        // prescaled INTT of d_t, limb 0
+    u64 *ext;                            // ModUp output tuple of (t, digit), slot 0
+    const u64 *consts;                   // [alpha][L+K] constants of (level, digit)
+    int level, beta;
+};
+
+struct MacJob {                          // the key MAC of one product
+    const u64 *d;                        // D tuple (NTT domain), polynomial t at d + t dstride
+    i64 dstride;
+    const u64 *ext;                      // ModUp output (t, digit) at ext + ((t-2) nd + digit) estride
+    i64 estride;
+    u64 *acc;                            // [2][level + K] accumulators, polynomial stride astride
+    i64 astride;
+    int level, n, nd, pad;
+};
+
+struct MacTarget {                       // one accumulator limb x of product `job`
+    int job, x;
+};
+
 cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st);
+cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_jobs, int maxt, int max_level,
+                                double bytes, cudaStream_t st);
+cudaError_t launch_rschain_table(const Context &C, const RsJob *jobs, int n_jobs, int max_polys, double bytes,
+                                 cudaStream_t st);
+cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_jobs, double bytes, double macs,
+                               cudaStream_t st);
+cudaError_t launch_mac_table(const Context &C, const MacJob *jobs, const MacTarget *targets, int n_targets,
+                             const u64 *keys, double bytes, double macs, cudaStream_t st);
 cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st);
 cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st);
 cudaError_t launch_rschain(const Context &C, const RsChainArgs &A, cudaStream_t st);

@@ -216,7 +216,7 @@ def peak(args):
         q = synth.prime_chain(bits, 1)[0]
         for kind in G.PEAK_KINDS:
             best = 0.0
-            for per_sm in (4, 8, 16):
+            for per_sm in (1, 2, 4, 8, 16):
                 r = G.peak_int(kind, q, blocks=sms * per_sm, threads=256, iters=2048)
                 best = max(best, r)
                 res["rates"][f"{kind}/{bits}bit/{per_sm}x256 per SM"] = round(r / 1e9, 2)
