@@ -304,16 +304,18 @@ int ckks_mul_k_requests(ckks_context *ctx, const ckks_request *req, uint32_t n, 
  * ckks_wave_create validates the items (as ckks_mul_k) and keeps their
  * pointers (the wave borrows them: inputs and outputs must stay allocated
  * while it is used); CKKS_EINVAL also for N <= 256 and for two items sharing
- * one output. ckks_wave_workspace_size gives the bytes of the caller's
- * device workspace (job tables, then every product's scratch).
- * ckks_wave_run enqueues the wave on `stream` (256-byte aligned workspace);
- * the first run with a given workspace writes the job tables into it with
- * one host-to-device copy on the stream (later runs with the same workspace
- * reuse them), so that first run should not be inside a stream capture.
- * ckks_wave_describe returns the number of launches of a run and the number
- * of inner-node heights (valid after the first run). ckks_wave_destroy
- * waits for the wave's table copy, if one is in flight, and frees its host
- * staging buffer. No device memory is allocated by the library. */
+ * one output. ckks_wave_workspace_size gives the bytes of the two device
+ * buffers a run needs: the job tables and the products' scratch. Waves run
+ * one after another on one stream may share a scratch buffer; each keeps
+ * its own table buffer. ckks_wave_run enqueues the wave on `stream` (both
+ * buffers 256-byte aligned); the first run with a given pair of buffers
+ * writes the job tables with one host-to-device copy on the stream (later
+ * runs with the same pair reuse them), so that first run should not be
+ * inside a stream capture. ckks_wave_describe returns the number of
+ * launches of a run and the number of inner-node heights (valid after the
+ * first run). ckks_wave_destroy waits for the wave's table copy, if one is
+ * in flight, and frees its host staging buffer. No device memory is
+ * allocated by the library. */
 typedef struct ckks_wave ckks_wave;
 typedef struct {
     const ckks_tuple *ct;       /* k input ciphertexts */
@@ -323,8 +325,8 @@ typedef struct {
 } ckks_wave_item;
 int ckks_wave_create(ckks_context *ctx, const ckks_wave_item *items, uint32_t n, const ckks_evk_set *evk,
                      ckks_wave **out);
-int ckks_wave_workspace_size(const ckks_wave *w, size_t *bytes);
-int ckks_wave_run(ckks_wave *w, void *workspace, size_t ws_bytes, void *stream);
+int ckks_wave_workspace_size(const ckks_wave *w, size_t *table_bytes, size_t *scratch_bytes);
+int ckks_wave_run(ckks_wave *w, void *tables, size_t table_bytes, void *scratch, size_t scratch_bytes, void *stream);
 int ckks_wave_describe(const ckks_wave *w, uint32_t *n_launches, uint32_t *heights);
 void ckks_wave_destroy(ckks_wave *w);
 

@@ -523,14 +523,23 @@ class Wave:
         _check(lib().ckks_wave_create(ctx._h, arr, len(items), evk._h, ctypes.byref(h)), "ckks_wave_create")
         self._h = h
 
-    def workspace_size(self) -> int:
-        n = ctypes.c_size_t()
-        _check(lib().ckks_wave_workspace_size(self._h, ctypes.byref(n)), "ckks_wave_workspace_size")
-        return n.value
+    def workspace_size(self) -> tuple:
+        """(table bytes, scratch bytes) of the two device buffers a run needs."""
+        t, n = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().ckks_wave_workspace_size(self._h, ctypes.byref(t), ctypes.byref(n)), "ckks_wave_workspace_size")
+        return t.value, n.value
 
-    def run(self, workspace, stream=None):
-        _check(lib().ckks_wave_run(self._h, workspace.data_ptr(), workspace.numel() * workspace.element_size(),
-                                   _stream(stream)), "ckks_wave_run")
+    def buffers(self, device="cuda"):
+        """Freshly allocated (tables, scratch) uint64 device buffers of the needed sizes."""
+        import torch
+        t, n = self.workspace_size()
+        return (torch.empty(max(1, t // 8 + 32), dtype=torch.uint64, device=device),
+                torch.empty(max(1, n // 8 + 32), dtype=torch.uint64, device=device))
+
+    def run(self, tables, scratch, stream=None):
+        _check(lib().ckks_wave_run(self._h, tables.data_ptr(), tables.numel() * tables.element_size(),
+                                   scratch.data_ptr(), scratch.numel() * scratch.element_size(), _stream(stream)),
+               "ckks_wave_run")
         for out, o in self.outs:
             out.level, out.n_polys, out.ntt_form, out.scale, out.poly_stride = (o.level, o.n_polys, o.ntt_form,
                                                                                 o.scale, o.poly_stride)

@@ -83,8 +83,8 @@ SIGNATURES = {
     "ckks_strerror": [I],
     "ckks_peak_chains": [],
     "ckks_wave_create": [V, V, U32, V, V],
-    "ckks_wave_workspace_size": [V, V],
-    "ckks_wave_run": [V, V, SZ, V],
+    "ckks_wave_workspace_size": [V, V, V],
+    "ckks_wave_run": [V, V, SZ, V, SZ, V],
     "ckks_wave_describe": [V, V, V],
     "ckks_wave_destroy": [V],
     "ckks_peak_int": [I, ctypes.c_uint64, V, V, I, I, I, V, V],

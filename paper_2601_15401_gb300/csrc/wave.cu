@@ -16,11 +16,13 @@
 // k and levels therefore takes a fixed number of launches:
 // heights x 6 + 14 (+ one tensor launch per tuple-size class).
 //
-// Memory: the caller's workspace holds the job tables (written on the first
-// run with that workspace, by one host-to-device copy on the run's stream)
-// followed by every product's own scratch (the same per-product layout as
-// ckks_mul_k with batch 1). Nothing is allocated on the device by the
-// library; the host staging buffer for the tables belongs to the wave.
+// Memory: two caller buffers, the job tables (written on the first run with
+// that pair of buffers, by one host-to-device copy on the run's stream) and
+// every product's own scratch (the same per-product layout as ckks_mul_k with
+// batch 1). Waves that run one after the other on a stream can share one
+// scratch buffer while each keeps its own (small) table buffer. Nothing is
+// allocated on the device by the library; the host staging buffer for the
+// tables belongs to the wave.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -89,7 +91,7 @@ struct ckks_wave {
     size_t scratch_bytes = 0;     // every product's scratch
     size_t table_bytes = 0;       // upper bound of the tables (sized by a dry build)
     // state of the last build
-    void *bound_ws = nullptr;
+    void *bound_tables = nullptr, *bound_scratch = nullptr;
     std::vector<Stage> stages;
     void *staging = nullptr;      // pinned host copy of the tables
     size_t staging_bytes = 0;
@@ -423,9 +425,9 @@ size_t put(std::vector<char> &buf, const std::vector<T> &v) {
     return off;
 }
 
-// Builds the stage list of a wave for a workspace at `ws` (device address
-// of its first byte): tables first, then the products' scratch.
-int build(ckks_wave &W, char *ws, std::vector<char> &tables) {
+// Builds the stage list and the job tables of a wave whose products' scratch
+// starts at device address `scratch`.
+int build(ckks_wave &W, char *scratch, std::vector<char> &tables) {
     const Context &C = W.ctx->c;
     int H = 0;
     for (const WaveProduct &w : W.items) {
@@ -433,7 +435,7 @@ int build(ckks_wave &W, char *ws, std::vector<char> &tables) {
         H = std::max(H, node_heights(*w.plan, h));
     }
     Builder B{C, W.evk->keys, H, {}};
-    Bump bump{ws + W.table_bytes, 0};
+    Bump bump{scratch, 0};
     for (const WaveProduct &w : W.items) build_product(B, w, bump);
     W.stages.clear();
     tables.clear();
@@ -459,7 +461,7 @@ int build(ckks_wave &W, char *ws, std::vector<char> &tables) {
     return CKKS_OK;
 }
 
-cudaError_t enqueue(ckks_wave &W, char *ws, cudaStream_t st) {
+cudaError_t enqueue(ckks_wave &W, char *ws /* the job tables */, cudaStream_t st) {
     const Context &C = W.ctx->c;
     for (const Stage &s : W.stages) {
         cudaError_t e = cudaSuccess;
@@ -481,7 +483,7 @@ cudaError_t enqueue(ckks_wave &W, char *ws, cudaStream_t st) {
             break;
         case SK_MAC:
             e = launch_mac_table(C, (const MacJob *)(ws + s.off), (const MacTarget *)(ws + s.off2), n, W.evk->keys,
-                                 s.bytes + (double)n * 0, s.ops, st);
+                                 s.bytes, s.ops, st);
             break;
         }
         if (e != cudaSuccess) return e;
@@ -565,7 +567,7 @@ int ckks_wave_create(ckks_context *ctx, const ckks_wave_item *items, uint32_t n,
     W->table_bytes = (size_t)1 << 30;  // provisional: measured below
     std::vector<char> tables;
     int rc = build(*W, (char *)(size_t)4096, tables);
-    W->table_bytes = align256(tables.size()) + 4096;
+    W->table_bytes = align256(tables.size());
     W->stages.clear();
     if (rc != CKKS_OK) {
         delete W;
@@ -575,9 +577,10 @@ int ckks_wave_create(ckks_context *ctx, const ckks_wave_item *items, uint32_t n,
     return CKKS_OK;
 }
 
-int ckks_wave_workspace_size(const ckks_wave *w, size_t *bytes) {
-    if (!w || !bytes) return CKKS_EINVAL;
-    *bytes = w->table_bytes + w->scratch_bytes;
+int ckks_wave_workspace_size(const ckks_wave *w, size_t *table_bytes, size_t *scratch_bytes) {
+    if (!w || !table_bytes || !scratch_bytes) return CKKS_EINVAL;
+    *table_bytes = w->table_bytes;
+    *scratch_bytes = w->scratch_bytes;
     return CKKS_OK;
 }
 
@@ -588,41 +591,43 @@ int ckks_wave_describe(const ckks_wave *w, uint32_t *n_launches, uint32_t *heigh
     return CKKS_OK;
 }
 
-int ckks_wave_run(ckks_wave *w, void *workspace, size_t ws_bytes, void *stream) {
-    if (!w || !workspace) return CKKS_EINVAL;
-    if (ws_bytes < w->table_bytes + w->scratch_bytes) return CKKS_ENOMEM;
-    if ((size_t)workspace % 256) return CKKS_EINVAL;
+int ckks_wave_run(ckks_wave *w, void *tables, size_t table_bytes, void *scratch, size_t scratch_bytes,
+                  void *stream) {
+    if (!w || !tables || !scratch) return CKKS_EINVAL;
+    if (table_bytes < w->table_bytes || scratch_bytes < w->scratch_bytes) return CKKS_ENOMEM;
+    if ((size_t)tables % 256 || (size_t)scratch % 256) return CKKS_EINVAL;
     ckks_context *ctx = w->ctx;
     const Context &C = ctx->c;
     if (C.sticky.load() != 0) return CKKS_ECUDA;
     cudaSetDevice(C.device);
     cudaStream_t st = (cudaStream_t)stream;
-    if (w->bound_ws != workspace) {
-        std::vector<char> tables;
-        int rc = build(*w, (char *)workspace, tables);
+    if (w->bound_tables != tables || w->bound_scratch != scratch) {
+        std::vector<char> host;
+        int rc = build(*w, (char *)scratch, host);
         if (rc != CKKS_OK) return rc;
         cudaError_t e = cudaSuccess;
         if (w->uploaded) e = cudaEventSynchronize(w->uploaded);  // the previous copy has left the staging buffer
-        if (e == cudaSuccess && w->staging_bytes < tables.size()) {
+        if (e == cudaSuccess && w->staging_bytes < host.size()) {
             if (w->staging) cudaFreeHost(w->staging);
             w->staging = nullptr;
             w->staging_bytes = 0;
-            e = cudaMallocHost(&w->staging, tables.size());
-            if (e == cudaSuccess) w->staging_bytes = tables.size();
+            e = cudaMallocHost(&w->staging, host.size());
+            if (e == cudaSuccess) w->staging_bytes = host.size();
         }
         if (e == cudaSuccess && !w->uploaded) e = cudaEventCreateWithFlags(&w->uploaded, cudaEventDisableTiming);
-        if (e == cudaSuccess) {
-            memcpy(w->staging, tables.data(), tables.size());
-            e = cudaMemcpyAsync(workspace, w->staging, tables.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !host.empty()) {
+            memcpy(w->staging, host.data(), host.size());
+            e = cudaMemcpyAsync(tables, w->staging, host.size(), cudaMemcpyHostToDevice, st);
         }
         if (e == cudaSuccess) e = cudaEventRecord(w->uploaded, st);
         if (e != cudaSuccess) {
             ctx->c.sticky.store((int)e);
             return CKKS_ECUDA;
         }
-        w->bound_ws = workspace;
+        w->bound_tables = tables;
+        w->bound_scratch = scratch;
     }
-    cudaError_t e = enqueue(*w, (char *)workspace, st);
+    cudaError_t e = enqueue(*w, (char *)tables, st);
     if (e != cudaSuccess) {
         ctx->c.sticky.store((int)e);
         return CKKS_ECUDA;

@@ -1,14 +1,19 @@
 """Batched execution of uneven k-input multiplications in one CUDA graph.
 
 A workload is a list of requests, each a k-input product at its own ring
-degree N, input level and k. Requests with the same (N, k, level,
-partition) form a group that runs as one batched library call
-(ckks_mul_k_batch: every kernel launch covers the whole group). Groups are
-spread over several streams so that small groups run side by side, and the
-whole schedule is captured once into a CUDA graph; replaying it launches the
-entire workload with one cudaGraphLaunch. Each stream owns one workspace
-sized for the largest group it runs (stream order makes reuse safe), so
-nothing is allocated while the graph runs.
+degree N, input level and k. Two executors:
+
+* WaveExecutor (cross-shape): the requests of one ring degree form waves of
+  any mix of k, level and partition; every stage of all products of a wave
+  is one launch (ckks_wave_*, device job tables), so a wave of 128 products
+  takes a few dozen launches whatever its mix.
+* BatchExecutor (per shape): requests with the same (N, k, level,
+  partition) form a group that runs as one batched library call
+  (ckks_mul_k_batch); groups are spread over several streams.
+
+Either schedule is captured once into a CUDA graph; replaying it launches
+the entire workload with one cudaGraphLaunch. Workspaces are allocated up
+front, so nothing is allocated while the graph runs.
 
 The library calls are the only device work; this module only arranges
 buffers, streams and the graph.
@@ -132,6 +137,101 @@ class BatchExecutor:
 
     def capture(self):
         """Capture the whole schedule into one CUDA graph."""
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=self.device)
+        with torch.cuda.graph(g, stream=cap):
+            self._enqueue(cap)
+        self.graph = g
+        torch.cuda.synchronize(self.device)
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+
+class WaveExecutor:
+    """Uneven requests as cross-shape waves (ckks_wave_*): the requests of
+    one ring degree are split, in order, into waves of at most `max_wave`
+    products of any k, level and partition; each wave runs every stage of
+    all its products as one launch per stage. The waves of one ring degree
+    run one after another on that degree's stream and share one scratch
+    buffer (each keeps its own job-table buffer); ring degrees run side by
+    side. capture() records the whole schedule in one CUDA graph.
+    contexts: {log_n: (Context, EvkSet)} with keys up to the largest k."""
+
+    def __init__(self, contexts: dict, max_wave: int = 128, device=None):
+        self.contexts = contexts
+        self.max_wave = max_wave
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.waves = []          # (log_n, Wave, tables)
+        self.scratch = {}        # log_n -> buffer
+        self.streams = {}
+        self.slot_of = {}        # rid -> (inp tensor [k][2][level][N], out Tuple)
+        self.graph = None
+        self._first_run = True
+
+    def plan(self, requests: list[MulRequest]):
+        from . import Wave
+        by_n = defaultdict(list)
+        for r in requests:
+            by_n[r.log_n].append(r)
+        self.waves, self.scratch, self.slot_of = [], {}, {}
+        need = defaultdict(int)
+        for log_n, reqs in sorted(by_n.items()):
+            ctx, evk = self.contexts[log_n]
+            for i in range(0, len(reqs), self.max_wave):
+                items = []
+                for r in reqs[i:i + self.max_wave]:
+                    depth = ctx.plan_describe(r.k, r.partition)["depth"]
+                    inp = torch.empty((r.k, 2, r.level, ctx.N), dtype=torch.uint64, device=self.device)
+                    out = Tuple(torch.empty((2, r.level - depth, ctx.N), dtype=torch.uint64, device=self.device),
+                                2, r.level - depth, r.level - depth)
+                    self.slot_of[r.rid] = (inp, out)
+                    items.append(([Tuple(inp[u], 2, r.level, r.level) for u in range(r.k)], out, r.partition))
+                w = Wave(ctx, items, evk)
+                t, n = w.workspace_size()
+                tables = torch.empty(t // 8 + 32, dtype=torch.uint64, device=self.device)
+                self.waves.append((log_n, w, tables))
+                need[log_n] = max(need[log_n], n)
+        for log_n, n in need.items():
+            self.scratch[log_n] = torch.empty(n // 8 + 32, dtype=torch.uint64, device=self.device)
+            self.streams[log_n] = torch.cuda.Stream(device=self.device)
+        self.graph = None
+        self._first_run = True
+
+    def input_view(self, rid: int):
+        return self.slot_of[rid][0]
+
+    def output_view(self, rid: int):
+        return self.slot_of[rid][1].data
+
+    def launches(self) -> int:
+        return sum(w.describe()["launches"] for _, w, _ in self.waves)
+
+    def _enqueue(self, main: torch.cuda.Stream):
+        start = torch.cuda.Event()
+        start.record(main)
+        for s in self.streams.values():
+            s.wait_event(start)
+        for log_n, w, tables in self.waves:
+            w.run(tables, self.scratch[log_n], stream=self.streams[log_n])
+        for s in self.streams.values():
+            e = torch.cuda.Event()
+            e.record(s)
+            main.wait_event(e)
+
+    def run_eager(self):
+        self._enqueue(torch.cuda.current_stream(self.device))
+        self._first_run = False
+
+    def capture(self):
+        """Capture the schedule in one CUDA graph (after one eager run, which
+        writes every wave's job tables)."""
+        if self._first_run:
+            self.run_eager()
         torch.cuda.synchronize(self.device)
         g = torch.cuda.CUDAGraph()
         cap = torch.cuda.Stream(device=self.device)
@@ -292,6 +392,18 @@ def autotune(ctx: Context, evk, k: int = 8, batch: int = 4, reps: int = 3, cache
 # the uneven-batch measurement: 1024 products with k uniform in 2..12, N in
 # {2^14, 2^15, 2^16}, input level uniform in [k, 24], in one graph launch
 # ---------------------------------------------------------------------------
+def _time_replays(fn, reps: int) -> float:
+    fn()  # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def main():
     import argparse
     import numpy as np
@@ -301,10 +413,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--requests", type=int, default=1024)
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--max-wave", type=int, default=128)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--log-ns", default="14,15,16")
     ap.add_argument("--seed", type=int, default=4)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--skip-groups", action="store_true", help="time only the wave executor and one per launch")
     args = ap.parse_args()
     log_ns = [int(x) for x in args.log_ns.split(",")]
     contexts, pools = build_gpu_state(tuple(log_ns))
@@ -320,43 +434,48 @@ def main():
         level = int(g.integers(k, 25))
         reqs.append(MulRequest(log_n, k, level, None, i))
         srcs[i] = [int(x) for x in g.integers(0, pools[log_n].shape[0], size=k)]
+
+    def fill(ex):
+        for r in reqs:
+            src = pools[r.log_n].view(torch.int64)[srcs[r.rid]][:, :, :r.level]
+            ex.input_view(r.rid).view(torch.int64).copy_(src)
+        torch.cuda.synchronize()
+
+    res = {"workload": f"{args.requests} k-input products, k in 2..12, N in {[1 << x for x in log_ns]}, "
+                       "level in [k, 24], L=24x50-bit q, K=8x60-bit p, dnum=3", "tuning": tuned}
+    # cross-shape waves, one CUDA graph
+    wx = WaveExecutor(contexts, max_wave=args.max_wave)
+    wx.plan(reqs)
+    fill(wx)
+    wx.capture()
+    wave_ms = _time_replays(wx.replay, args.reps)
+    wave_out = {r.rid: wx.output_view(r.rid).clone() for r in reqs}
+    res.update({"waves": len(wx.waves), "wave_launches": wx.launches(), "wave_graph_ms": round(wave_ms, 3),
+                "wave_ctmults_s": round(args.requests / (wave_ms / 1e3), 1)})
+    del wx
+    torch.cuda.empty_cache()
+    # per-shape groups on several streams, one CUDA graph
     ex = BatchExecutor(contexts, n_streams=args.streams)
     ex.plan(reqs)
-    for r in reqs:
-        src = pools[r.log_n].view(torch.int64)[srcs[r.rid]][:, :, :r.level]
-        ex.input_view(r.rid).view(torch.int64).copy_(src)
-    torch.cuda.synchronize()
-    t_cap = torch.cuda.Event(enable_timing=True)
-    ex.capture()
-    ex.replay()  # warm
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.reps):
-        ex.replay()
-    e1.record()
-    e1.synchronize()
-    graph_ms = e0.elapsed_time(e1) / args.reps
-    graph_out = {r.rid: ex.output_view(r.rid).clone() for r in reqs}
+    fill(ex)
+    if not args.skip_groups:
+        ex.capture()
+        graph_ms = _time_replays(ex.replay, args.reps)
+        same_groups = all(torch.equal(wave_out[r.rid].view(torch.int64), ex.output_view(r.rid).view(torch.int64))
+                          for r in reqs)
+        res.update({"groups": len(ex.groups), "streams": args.streams, "group_graph_ms": round(graph_ms, 3),
+                    "group_ctmults_s": round(args.requests / (graph_ms / 1e3), 1),
+                    "waves_equal_groups": bool(same_groups)})
     # reference schedule: one product per library call, one stream, eager
-    ws = one_per_launch(contexts, reqs, ex)  # warm
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.reps):
-        one_per_launch(contexts, reqs, ex)
-    e1.record()
-    e1.synchronize()
-    single_ms = e0.elapsed_time(e1) / args.reps
-    same = all(torch.equal(graph_out[r.rid].view(torch.int64), ex.output_view(r.rid).view(torch.int64)) for r in reqs)
-    kernels = sum(len(g.tuples) > 0 for g in ex.groups)
-    print(json.dumps({
-        "workload": f"{args.requests} k-input products, k in 2..12, N in {[1 << x for x in log_ns]}, level in [k, 24], "
-                    "L=24x50-bit q, K=8x60-bit p, dnum=3",
-        "groups": len(ex.groups), "streams": args.streams,
-        "graph_ms": round(graph_ms, 3), "graph_ctmults_s": round(args.requests / (graph_ms / 1e3), 1),
-        "one_per_launch_ms": round(single_ms, 3),
-        "one_per_launch_ctmults_s": round(args.requests / (single_ms / 1e3), 1),
-        "speedup": round(single_ms / graph_ms, 3), "results_identical": bool(same), "tuning": tuned}))
+    single_ms = _time_replays(lambda: one_per_launch(contexts, reqs, ex), args.reps)
+    same = all(torch.equal(wave_out[r.rid].view(torch.int64), ex.output_view(r.rid).view(torch.int64)) for r in reqs)
+    res.update({"one_per_launch_ms": round(single_ms, 3),
+                "one_per_launch_ctmults_s": round(args.requests / (single_ms / 1e3), 1),
+                "waves_equal_one_per_launch": bool(same),
+                "speedup_waves_vs_one_per_launch": round(single_ms / wave_ms, 3)})
+    if "group_graph_ms" in res:
+        res["speedup_waves_vs_groups"] = round(res["group_graph_ms"] / wave_ms, 3)
+    print(json.dumps(res))
 
 
 if __name__ == "__main__":

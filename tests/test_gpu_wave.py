@@ -58,8 +58,8 @@ def _run_wave(S, items):
 
     import paper_2601_15401_gb300 as G
     w = G.Wave(S.ctx, [(it["cts"], it["out"], it["part"]) for it in items], S.evk)
-    ws = torch.empty(w.workspace_size() // 8 + 1, dtype=torch.uint64, device="cuda")
-    w.run(ws)
+    ws = w.buffers()
+    w.run(*ws)
     S.ctx.check()
     return w, ws
 
@@ -88,21 +88,20 @@ def test_wave_mixed_small_matches_oracle_and_alone(S_small):
 
 
 def test_wave_rerun_and_new_workspace(S_small):
-    """A second run with the same workspace reuses the tables; a run with
-    another workspace rebuilds them; both give the same residues."""
-    import torch
+    """A second run with the same buffers reuses the tables; a run with
+    other buffers rebuilds them; both give the same residues."""
     S = S_small
     items = _mix(S, 9, 2)
     w, ws = _run_wave(S, items)
     first = [host(it["out"].data) for it in items]
     for it in items:
         it["out"].data.zero_()
-    w.run(ws)
+    w.run(*ws)
     again = [host(it["out"].data) for it in items]
-    ws2 = torch.empty(w.workspace_size() // 8 + 64, dtype=torch.uint64, device="cuda")
+    t2, s2 = w.buffers()
     for it in items:
         it["out"].data.zero_()
-    w.run(ws2[32:])
+    w.run(t2[32:], s2[64:])  # other buffers (256-byte aligned offsets): the tables are rebuilt
     other = [host(it["out"].data) for it in items]
     S.ctx.check()
     for a, b, c in zip(first, again, other):
@@ -126,12 +125,25 @@ def test_wave_argument_errors(S_small):
     with pytest.raises(G.CkksError) as e:
         G.Wave(S.ctx, [(low, out, None)], S.evk)
     assert e.value.code == -2
-    # workspace too small
+    # buffers too small
     w = G.Wave(S.ctx, [(it["cts"], it["out"], it["part"]) for it in items], S.evk)
-    ws = torch.empty(w.workspace_size() // 8 - 64, dtype=torch.uint64, device="cuda")
+    t, n = w.workspace_size()
+    tb = torch.empty(t // 8 + 1, dtype=torch.uint64, device="cuda")
+    sb = torch.empty(n // 8 - 64, dtype=torch.uint64, device="cuda")
     with pytest.raises(G.CkksError) as e:
-        w.run(ws)
+        w.run(tb, sb)
     assert e.value.code == -4
+    # waves run one after the other may share one scratch buffer
+    other = _mix(S, 4, 4, other_parts=False)
+    w2 = G.Wave(S.ctx, [(it["cts"], it["out"], it["part"]) for it in other], S.evk)
+    shared = torch.empty(max(n, w2.workspace_size()[1]) // 8 + 1, dtype=torch.uint64, device="cuda")
+    t2 = torch.empty(w2.workspace_size()[0] // 8 + 1, dtype=torch.uint64, device="cuda")
+    w.run(tb, shared)
+    w2.run(t2, shared)
+    w.run(tb, shared)
+    for it in items + other:
+        alone, _ = _alone(S, it)
+        assert np.array_equal(host(it["out"].data), alone)
     S.ctx.check()
 
 
