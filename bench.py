@@ -180,7 +180,17 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     lat = {k: [] for k in ks}
     ex = None
-    if args.streams > 1:
+    wave = None
+    if args.engine == "waves":
+        # the whole step (every k, every batch element) as one cross-shape
+        # wave: each stage of all 144 products is one launch
+        wave = G.Wave(ctx, [(tup[k][b], otup[k][b], None) for k in ks for b in range(B)], evk)
+        wave_bufs = wave.buffers(dev)
+        ws = None
+        torch.cuda.empty_cache()
+        wave.run(*wave_bufs, stream=stream)  # writes the job tables
+        torch.cuda.synchronize()
+    elif args.streams > 1:
         # the step through the batched executor: one group per k, groups
         # spread over streams, the whole step captured in one CUDA graph
         from paper_2601_15401_gb300.executor import BatchExecutor, MulRequest
@@ -197,6 +207,9 @@ def run_ours(args, rank, world, local_rank):
     def step(record=False):
         if ex is not None:
             ex.replay()
+            return []
+        if wave is not None:
+            wave.run(*wave_bufs, stream=stream)
             return []
         evs = []
         for k in ks:
@@ -307,7 +320,20 @@ def run_ours(args, rank, world, local_rank):
     lat_all = [x for k in ks for x in lat[k]] or [ms_step]
     per_k = {}
     for k in ks:
-        xs = sorted(lat[k]) or [float("nan")]
+        if not lat[k]:
+            # the step ran as one wave: time each k's batched call alone
+            # (outside the timed region) for the per-k comparisons
+            wsk = torch.empty(ctx.workspace_size(k, L, B) // 8 + 1, dtype=torch.uint64, device=dev)
+            for r in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.mul_k_batch(tup[k], evk, otup[k], wsk, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                if r:
+                    lat[k].append(e0.elapsed_time(e1))
+            del wsk
+        xs = sorted(lat[k])
         per_k[k] = {"batch_ms_p50": round(statistics.median(xs), 3), "kinput_ctmults_s": round(B / (statistics.median(xs) / 1e3), 1)}
 
     result = {
@@ -316,7 +342,9 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded uniform residues, seeded key draws)",
         "config": dict(CONFIG, ks=ks, batch_per_k=B, products_per_step=B * len(ks),
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                       executor=f"CUDA graph, {args.streams} streams" if args.streams > 1 else "one stream, eager"),
+                       executor=("one cross-shape wave per step (every stage of all products one launch)"
+                                 if args.engine == "waves" else
+                                 f"CUDA graph, {args.streams} streams" if args.streams > 1 else "one stream, eager")),
         "gpu_launches": int(launches),
         "latency_ms": {"per_batch_p50": round(statistics.median(lat_all), 3),
                        "per_batch_p99": round(sorted(lat_all)[max(0, math.ceil(0.99 * len(lat_all)) - 1)], 3)},
@@ -358,8 +386,16 @@ def run_ours(args, rank, world, local_rank):
         # the comparator legs leave large cached device blocks behind; release
         # them before the host-buffer leg (measured on one box: uploads ran at
         # 69-87 GB/s with those blocks cached and 210.7 GB/s after release)
+        if wave is not None:
+            # the host-buffer leg pipelines uploads with the multiplies per k:
+            # it runs the batched calls (same residues as the wave)
+            del wave_bufs
+            wave.close()
         torch.cuda.empty_cache()
         if ex is None:
+            if ws is None:
+                ws = torch.empty(max(ctx.workspace_size(k, L, B) for k in ks) // 8 + 1, dtype=torch.uint64,
+                                 device=dev)
             result["e2e"] = e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, inp, outs, tup, otup,
                                     inp[max(ks)].clone())
 
@@ -539,6 +575,14 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
         t1.synchronize()
         return h2d / (t0.elapsed_time(t1) / 1e3) / 1e9
 
+    # the first host-to-device passes over freshly pinned buffers run at a
+    # fraction of the link's rate (measured: 86 GB/s on the first pass, 210
+    # GB/s later on one box); pass over them until the rate settles
+    warm_bw = [upload_alone()]
+    for _ in range(4):
+        if len(warm_bw) > 1 and warm_bw[-1] > 0.9 * max(warm_bw[:-1]):
+            break
+        warm_bw.append(upload_alone())
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -558,6 +602,7 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     return {"value": round(B * len(ks) * world / (ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3),
             "h2d_GBps_alone": [round(bw_before, 1), round(bw_after, 1)],
+            "h2d_GBps_warmup": [round(x, 1) for x in warm_bw],
             "copy_streams": len(copies), "host_numa": numa_note,
             "overlap": "uploads (own stream) overlap the multiplies of this and the previous step; downloads on "
                        "a second stream"}
@@ -654,6 +699,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--streams", type=int, default=1)
+    ap.add_argument("--engine", default="batch", choices=["batch", "waves"],
+                    help="batch: one batched call per k; waves: the whole step as one cross-shape wave")
     args = ap.parse_args()
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)

@@ -42,10 +42,6 @@ static int phase_geometry(const Context &C, bool cols, NttPhase &P, PhaseLaunch 
         G.tiles = P.N1 / n_sub;
         G.smem = (size_t)n_sub * (n + n / 16) * sizeof(u64);
     }
-#if CKKS_NTT_STW
-    // twiddle rows after the data: one row for columns, one per block
-    G.smem = (G.smem + 15) / 16 * 16 + (size_t)(cols ? 1 : n_sub) * (1 << logn) * sizeof(ulonglong2);
-#endif
     P.sub_per_tile = n_sub;
     P.log_sub = 0;
     while ((1 << P.log_sub) < n_sub) ++P.log_sub;

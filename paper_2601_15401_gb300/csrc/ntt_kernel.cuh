@@ -71,17 +71,6 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
 #ifndef CKKS_NTT_RMAX
 #define CKKS_NTT_RMAX 4
 #endif
-// 1: a tile's twiddles are copied into shared memory with its data (one
-// coalesced copy per tile instead of a dependent global load per butterfly)
-#ifndef CKKS_NTT_STW
-#define CKKS_NTT_STW 1
-#endif
-
-// Shared-memory words of a tile's data (the twiddle rows follow it).
-template <bool COLS, int LOGN>
-__host__ __device__ __forceinline__ int tile_data_words(int n_sub) {
-    return COLS ? (n_sub << LOGN) : n_sub * ((1 << LOGN) + ((1 << LOGN) >> 4));
-}
 template <int LOGN, int P>
 struct Pass {
     static constexpr int NP = (LOGN + CKKS_NTT_RMAX - 1) / CKKS_NTT_RMAX;
@@ -295,8 +284,6 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
                 x[k] = sm[lay.off(sp, pt)];
             }
         }
-        // staged twiddles: entry m + i of the sub-problem's row of n; else the
-        // global table's index m (N1 + block) + i
         const int twb = tw_b0 + tw_bmul * sp;
         if (FWD) {
 #pragma unroll
@@ -307,7 +294,7 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
                 for (int k = 0; k < EL; ++k) {
                     if ((k & h) == 0) {
                         const int i = (g << ep) + (k >> (R - ep));
-                        ct_bfly(x[k], x[k + h], tw[CKKS_NTT_STW ? twb + m + i : m * twb + i], q);
+                        ct_bfly(x[k], x[k + h], tw[m * twb + i], q);
                     }
                 }
             }
@@ -320,7 +307,7 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
                 for (int k = 0; k < EL; ++k) {
                     if ((k & h) == 0) {
                         const int i = (g << ep) + (k >> (R - ep));
-                        gs_bfly(x[k], x[k + h], tw[CKKS_NTT_STW ? twb + m + i : m * twb + i], q);
+                        gs_bfly(x[k], x[k + h], tw[m * twb + i], q);
                     }
                 }
             }
@@ -340,10 +327,16 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
 
 // Direct global access is used on a side whose pass reads / writes at
 // least 8 consecutive words per sub-problem (always true for column tiles).
+// CKKS_NTT_DIRECT_IN = 0 stages every tile through shared memory on the
+// load side (batched loads), keeping direct global stores.
+#ifndef CKKS_NTT_DIRECT_IN
+#define CKKS_NTT_DIRECT_IN 1
+#endif
 template <int LOGN, bool COLS, int P>
 struct PassAccess {
     static constexpr int t_min = (1 << LOGN) >> (Pass<LOGN, P>::start + Pass<LOGN, P>::len);
     static constexpr bool direct = COLS || t_min >= 8;
+    static constexpr bool direct_in = direct && CKKS_NTT_DIRECT_IN;
 };
 
 template <int LOGN, bool FWD, bool COLS, int LM, int SM, int I>
@@ -354,7 +347,7 @@ __device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS, LOGN> &la
     if constexpr (I < NP) {
         constexpr int PP = FWD ? I : NP - 1 - I;
         constexpr bool first = I == 0, last = I == NP - 1;
-        constexpr bool gin = first && PassAccess<LOGN, COLS, PP>::direct;
+        constexpr bool gin = first && PassAccess<LOGN, COLS, PP>::direct_in;
         constexpr bool gout = last && PassAccess<LOGN, COLS, PP>::direct;
         run_pass<LOGN, Pass<LOGN, PP>::len, Pass<LOGN, PP>::start, FWD, COLS, gin, gout, LM, SM>(
             sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
@@ -375,31 +368,12 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
     const int t0 = tile << lsub;  // first column (COLS) or block (!COLS)
     constexpr int PF = FWD ? 0 : NP - 1;
     constexpr int PL = FWD ? NP - 1 : 0;
-    constexpr bool gin = PassAccess<LOGN, COLS, PF>::direct;
+    constexpr bool gin = PassAccess<LOGN, COLS, PF>::direct_in;
     constexpr bool gout = PassAccess<LOGN, COLS, PL>::direct;
     const int total = n_sub << LOGN;
-#if CKKS_NTT_STW
-    // twiddle rows: columns share one row (entries 1..n-1 of the table);
-    // block sp's row holds entry m (N1 + t0 + sp) + i at m + i
-    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sm + tile_data_words<COLS, LOGN>(n_sub));
-    {
-        const int rows = COLS ? 1 : n_sub;
-        for (int idx = threadIdx.x; idx < (rows << LOGN); idx += blockDim.x) {
-            const int sp = idx >> LOGN, kk = idx & (n - 1);
-            if (kk == 0) continue;
-            const int m = 1 << (31 - __clz(kk));
-            stw[idx] = COLS ? tw[kk] : tw[(i64)m * (P.N1 + t0 + sp) + (kk - m)];
-        }
-    }
-    const ulonglong2 *twp = stw;
-    const int tw_b0 = 0;
-    const int tw_bmul = COLS ? 0 : n;
-#else
-    const ulonglong2 *twp = tw;
     // twiddle base: columns -> 1; blocks -> N1 + block
     const int tw_b0 = COLS ? 1 : P.N1 + t0;
     const int tw_bmul = COLS ? 0 : 1;
-#endif
     if (!gin) {
         // coalesced global -> shared with the fused load, eight loads in
         // flight per thread before their shared-memory stores
@@ -427,13 +401,9 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
                 }
             }
         }
+        __syncthreads();
     }
-#if CKKS_NTT_STW
-    __syncthreads();
-#else
-    if (!gin) __syncthreads();
-#endif
-    run_passes<LOGN, FWD, COLS, LM, SM, 0>(sm, lay, twp, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
+    run_passes<LOGN, FWD, COLS, LM, SM, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
     if (!gout) {
         // shared -> global with the fused store (coalesced)
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {

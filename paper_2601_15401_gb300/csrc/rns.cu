@@ -300,8 +300,77 @@ cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_job
 // Grid: x = coefficient chunk, y = target limb, z = batch (fastest-varying
 // batch would reuse key tiles in L2; see launch order below).
 // ---------------------------------------------------------------------------
+// Coefficients per thread of the key MAC: two adjacent coefficients read
+// with 16-byte loads (twice the bytes in flight per load instruction; the
+// kernel is bound by load latency, not by its multiplies).
+#ifndef CKKS_MAC_VEC
+#define CKKS_MAC_VEC 2
+#endif
+
+template <int V>
+__device__ __forceinline__ void load_span(const u64 *p, u64 (&o)[V]) {
+    if constexpr (V == 2) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) o[i] = p[i];
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void store_span(u64 *p, const u64 (&v)[V]) {
+    if constexpr (V == 2) {
+        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) p[i] = v[i];
+    }
+}
+
+// V coefficients of accumulator limb x of one product: dsrc / esrc point at
+// limb x, coefficient e of the D tuple / the first ModUp output; krow at the
+// prime's row, coefficient e, of the first key.
+template <int V>
+__device__ __forceinline__ void mac_span(const u64 *dsrc, i64 dstride, const u64 *esrc, i64 estride, int n, int nd,
+                                         int my_digit, const u64 *krow, i64 key_pstride, int key_digits, const ModQ m,
+                                         u64 *dst, i64 astride) {
+    const u64 q = m.q;
+    Acc128 a0[V], a1[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        a0[v].zero();
+        a1[v].zero();
+    }
+    for (int t = 2; t <= n; ++t) {
+        for (int beta = 0; beta < nd; ++beta) {
+            const u64 *src = beta == my_digit ? dsrc + (i64)t * dstride : esrc + (i64)((t - 2) * nd + beta) * estride;
+            const u64 *key = krow + ((i64)((t - 2) * key_digits + beta) * 2) * key_pstride;
+            u64 tv[V], k0[V], k1[V];
+            load_span<V>(src, tv);
+            load_span<V>(key, k0);
+            load_span<V>(key + key_pstride, k1);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                a0[v].mac(tv[v], k0[v], q);
+                a1[v].mac(tv[v], k1[v], q);
+            }
+        }
+    }
+    u64 r0[V], r1[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        r0[v] = redc(a0[v].hi, a0[v].lo, m);
+        r1[v] = redc(a1[v].hi, a1[v].lo, m);
+    }
+    store_span<V>(dst, r0);
+    store_span<V>(dst + astride, r1);
+}
+
 __global__ void __launch_bounds__(1024) mac_kernel(MacArgs A) {
-    const int chunks = (A.N + blockDim.x - 1) / blockDim.x;
+    constexpr int V = CKKS_MAC_VEC;
+    const int chunks = (A.N + blockDim.x * V - 1) / (blockDim.x * V);
     // block order: batch fastest, then chunk, then limb -> blocks that share a
     // key tile run next to each other
     int bid = blockIdx.x;
@@ -309,38 +378,19 @@ __global__ void __launch_bounds__(1024) mac_kernel(MacArgs A) {
     bid /= A.n_batch;
     const int chunk = bid % chunks;
     const int x = bid / chunks;  // acc slot: Q limbs 0..level-1 then P limbs
-    const int e = chunk * blockDim.x + threadIdx.x;
+    const int e = (chunk * blockDim.x + threadIdx.x) * V;
     if (e >= A.N) return;
     const bool isq = x < A.level;
     const int prime = isq ? x : A.L + (x - A.level);
-    const ModQ m = A.mods[prime];
-    const u64 q = m.q;
-    const int my_digit = isq ? x / A.alpha : -1;
-    Acc128 acc0, acc1;
-    acc0.zero();
-    acc1.zero();
-    const i64 key_row = (i64)prime * A.N + e;
-    for (int t = 2; t <= A.n; ++t) {
-        for (int beta = 0; beta < A.n_digits; ++beta) {
-            u64 term;
-            if (beta == my_digit)
-                term = A.d.ptr[(i64)b * A.d.bstride + (i64)t * A.d.pstride + (i64)x * A.N + e];
-            else
-                term = A.ext.ptr[(i64)b * A.ext.bstride + (i64)((t - 2) * A.n_digits + beta) * A.ext.pstride +
-                                 (i64)x * A.N + e];
-            const u64 *key = A.keys + ((i64)((t - 2) * A.key_digits + beta) * 2) * A.key_pstride;
-            acc0.mac(term, key[key_row], q);
-            acc1.mac(term, key[A.key_pstride + key_row], q);
-        }
-    }
-    u64 *dst = A.acc.ptr + (i64)b * A.acc.bstride + (i64)x * A.N + e;
-    dst[0] = redc(acc0.hi, acc0.lo, m);
-    dst[A.acc.pstride] = redc(acc1.hi, acc1.lo, m);
+    const i64 off = (i64)x * A.N + e;
+    mac_span<V>(A.d.ptr + (i64)b * A.d.bstride + off, A.d.pstride, A.ext.ptr + (i64)b * A.ext.bstride + off,
+                A.ext.pstride, A.n, A.n_digits, isq ? x / A.alpha : -1, A.keys + (i64)prime * A.N + e, A.key_pstride,
+                A.key_digits, A.mods[prime], A.acc.ptr + (i64)b * A.acc.bstride + off, A.acc.pstride);
 }
 
 cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
     const int thr = C.tune_mac_threads;
-    const int chunks = (A.N + thr - 1) / thr;
+    const int chunks = (A.N + thr * CKKS_MAC_VEC - 1) / (thr * CKKS_MAC_VEC);
     long long blocks = (long long)chunks * (A.level + A.K) * A.n_batch;
     count_kernel(C);
     // per batch element: (n-1) * digits terms and 2 outputs per target limb;
@@ -360,40 +410,24 @@ cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
 __global__ void __launch_bounds__(1024) mac_table_kernel(const MacJob *jobs, const MacTarget *targets, const u64 *keys,
                                                          i64 key_pstride, int key_digits, int alpha, int L, int N,
                                                          const ModQ *mods) {
+    constexpr int V = CKKS_MAC_VEC;
     const MacTarget T = targets[blockIdx.x];
     const MacJob J = jobs[T.job];
-    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    const int e = (blockIdx.y * blockDim.x + threadIdx.x) * V;
     if (e >= N) return;
     const int x = T.x;
     const bool isq = x < J.level;
     const int prime = isq ? x : L + (x - J.level);
-    const ModQ m = mods[prime];
-    const u64 q = m.q;
-    const int my_digit = isq ? x / alpha : -1;
-    Acc128 acc0, acc1;
-    acc0.zero();
-    acc1.zero();
-    const i64 key_row = (i64)prime * N + e;
     const i64 off = (i64)x * N + e;
-    for (int t = 2; t <= J.n; ++t) {
-        for (int beta = 0; beta < J.nd; ++beta) {
-            const u64 term = beta == my_digit ? J.d[(i64)t * J.dstride + off]
-                                              : J.ext[(i64)((t - 2) * J.nd + beta) * J.estride + off];
-            const u64 *key = keys + ((i64)((t - 2) * key_digits + beta) * 2) * key_pstride;
-            acc0.mac(term, key[key_row], q);
-            acc1.mac(term, key[key_pstride + key_row], q);
-        }
-    }
-    u64 *dst = J.acc + off;
-    dst[0] = redc(acc0.hi, acc0.lo, m);
-    dst[J.astride] = redc(acc1.hi, acc1.lo, m);
+    mac_span<V>(J.d + off, J.dstride, J.ext + off, J.estride, J.n, J.nd, isq ? x / alpha : -1,
+                keys + (i64)prime * N + e, key_pstride, key_digits, mods[prime], J.acc + off, J.astride);
 }
 
 cudaError_t launch_mac_table(const Context &C, const MacJob *jobs, const MacTarget *targets, int n_targets,
                              const u64 *keys, double bytes, double macs, cudaStream_t st) {
     if (n_targets <= 0) return cudaSuccess;
     const int thr = C.tune_mac_threads;
-    const int chunks = (C.N + thr - 1) / thr;
+    const int chunks = (C.N + thr * CKKS_MAC_VEC - 1) / (thr * CKKS_MAC_VEC);
     if (chunks > 65535) return cudaErrorInvalidValue;
     count_kernel(C);
     ProfScope ps(C, KC_MAC, bytes, st, macs);

@@ -34,7 +34,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "chain3", "rotate", "encode", "decode", "precision",
-                                         "peak"], default="ntt")
+                                         "peak", "tensor_rates"], default="ntt")
     ap.add_argument("--log-n", type=int, default=16)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--k", type=int, default=8)
@@ -57,6 +57,8 @@ def main():
         return precision(args)
     if args.op == "peak":
         return peak(args)
+    if args.op == "tensor_rates":
+        return tensor_rates(args)
     if args.params == "small":
         p = synth.params_small(log_n=args.log_n)
     elif args.params == "mid":
@@ -203,6 +205,40 @@ def main():
         "kernels": {n: {"launches": v["launches"], "avg_us": round(v["total_ms"] * 1e3 / v["launches"], 2),
                         "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1),
                         "Gops": round(v["int_ops"] / (v["total_ms"] / 1e3) / 1e9, 2)} for n, v in prof.items()}}))
+
+
+def tensor_rates(args):
+    """Dense tensor-core rates of this GPU through the vendor GEMMs (context
+    for the BConv-as-GEMM question: an exact byte-split BConv would run as
+    an INT8 GEMM with int32 accumulation): int8 x int8 -> int32
+    (torch._int_mm) and bf16 (torch.matmul), 8192^3, best of 10 after
+    warm-up, CUDA events."""
+    import torch
+    n = 8192
+    res = {"op": "tensor_rates", "gpu": torch.cuda.get_device_name(0), "shape": [n, n, n]}
+
+    def best(fn, flops):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return round(flops / (min(ms) / 1e3) / 1e12, 1)
+    a8 = torch.randint(-128, 127, (n, n), dtype=torch.int8, device="cuda")
+    b8 = torch.randint(-128, 127, (n, n), dtype=torch.int8, device="cuda")
+    try:
+        res["int8_tops"] = best(lambda: torch._int_mm(a8, b8), 2.0 * n ** 3)
+    except Exception as e:  # no int8 GEMM in this torch build
+        res["int8_error"] = str(e)[:200]
+    ab = torch.randn((n, n), dtype=torch.bfloat16, device="cuda")
+    bb = torch.randn((n, n), dtype=torch.bfloat16, device="cuda")
+    res["bf16_tflops"] = best(lambda: ab @ bb, 2.0 * n ** 3)
+    print(json.dumps(res))
 
 
 def peak(args):

@@ -70,6 +70,10 @@ class Scheduler:
     def __init__(self, backend, cap_bytes: int, max_batch: int = 8, max_queue: int = 100000,
                  timeout_s: float | None = None):
         self.be = backend
+        # requests that may share a batch: the backend's grouping key if it
+        # has one (cross-shape batches group by ring degree only), else the
+        # full shape (N, k, level, partition)
+        self.key = getattr(backend, "group_key", None) or (lambda r: r.shape)
         self.timeout_s = timeout_s      # watchdog: a batch running longer is failed
         self.failed: list[Request] = []
         self.cap = cap_bytes
@@ -88,7 +92,7 @@ class Scheduler:
         if sum(len(q) for q in self.queues.values()) >= self.max_queue:
             self.rejected += 1
             return False
-        self.queues.setdefault(r.shape, deque()).append(r)
+        self.queues.setdefault(self.key(r), deque()).append(r)
         return True
 
     def pending(self) -> int:
@@ -140,14 +144,23 @@ class Scheduler:
             q = self.queues[shape]
             n = min(len(q), self.max_batch)
             fits = getattr(self.be, "fits", None)
-            while n > 0 and (self.in_use + self.be.footprint(shape, n) > self.cap or (fits and not fits(shape, n))):
+            by_reqs = getattr(self.be, "footprint_reqs", None)
+
+            def fp_of(n):
+                return by_reqs([q[i] for i in range(n)]) if by_reqs else self.be.footprint(shape, n)
+
+            def fits_n(n):
+                if not fits:
+                    return True
+                return fits([q[i] for i in range(n)]) if by_reqs else fits(shape, n)
+            while n > 0 and (self.in_use + fp_of(n) > self.cap or not fits_n(n)):
                 n -= 1
             if n == 0:
                 break  # wait for memory to free up
+            fp = fp_of(n)
             reqs = [q.popleft() for _ in range(n)]
             if not q:
                 del self.queues[shape]
-            fp = self.be.footprint(shape, n)
             b = Batch(self.next_bid, shape, reqs, self.free_streams.popleft(), fp)
             self.next_bid += 1
             for r in reqs:
@@ -256,6 +269,99 @@ class GpuBackend:
             out = b.handle[2]
             for i, r in enumerate(b.reqs):
                 self.results[r.rid] = out[i]
+        b.handle = None
+
+
+class WaveBackend:
+    """Cross-shape batches: the pending requests of one ring degree, any mix
+    of k, level and partition, run as one wave (ckks_wave_*: every stage of
+    every product in one launch). Inputs are read in place from the resident
+    pool (a wave item points at its pool ciphertexts, no gather); each batch
+    allocates only its outputs and its job tables; every stream owns a
+    scratch buffer of `ws_bytes` allocated up front, and a batch whose
+    scratch would not fit it runs with fewer requests.
+
+    contexts: {log_n: (Context, EvkSet)}, pools: {log_n: tensor [P][2][L][N]}."""
+
+    def __init__(self, contexts, pools, n_streams: int = 4, ws_bytes: int = 16 << 30, keep_results: bool = False):
+        import torch
+        self.torch = torch
+        self.contexts = contexts
+        self.pools = pools
+        self.n_streams = n_streams
+        self.keep_results = keep_results
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.ws_bytes = ws_bytes
+        self.scratch = [torch.empty(ws_bytes // 8, dtype=torch.uint64, device="cuda") for _ in range(n_streams)]
+        self.results = {}
+        self._need = {}
+
+    @staticmethod
+    def group_key(r: Request):
+        return (r.log_n,)
+
+    def resident_bytes(self) -> int:
+        return self.torch.cuda.memory_allocated()
+
+    def _req_bytes(self, r: Request) -> tuple:
+        """(scratch, output) bytes of one product (scratch as ckks_mul_k's
+        workspace for it alone, which is the wave's per-product layout)."""
+        key = (r.log_n, r.k, r.level, r.partition)
+        if key not in self._need:
+            ctx, _ = self.contexts[r.log_n]
+            depth = ctx.plan_describe(r.k, r.partition)["depth"]
+            self._need[key] = (ctx.workspace_size(r.k, r.level, 1, r.partition),
+                               2 * (r.level - depth) * ctx.N * 8)
+        return self._need[key]
+
+    def fits(self, reqs) -> bool:
+        return sum(self._req_bytes(r)[0] for r in reqs) <= self.ws_bytes
+
+    def footprint_reqs(self, reqs) -> int:
+        """Device bytes a batch allocates: its outputs (the job tables are
+        small; inputs stay in the pool)."""
+        return sum(self._req_bytes(r)[1] for r in reqs)
+
+    def footprint(self, shape, n: int) -> int:  # for the scheduler's fallback path
+        return 0
+
+    def launch(self, b: Batch):
+        torch = self.torch
+        from . import Tuple, Wave
+        (log_n,) = b.shape
+        ctx, evk = self.contexts[log_n]
+        pool = self.pools[log_n]
+        L = pool.shape[2]
+        st = self.streams[b.stream]
+        items, outs = [], []
+        with torch.cuda.stream(st):
+            for r in b.reqs:
+                depth = ctx.plan_describe(r.k, r.partition)["depth"]
+                ol = r.level - depth
+                out = Tuple(torch.empty((2, ol, ctx.N), dtype=torch.uint64, device=pool.device), 2, ol, ol)
+                outs.append(out)
+                items.append(([Tuple(pool[c], 2, r.level, L) for c in r.cts], out, r.partition))
+            w = Wave(ctx, items, evk)
+            t, _ = w.workspace_size()
+            tables = torch.empty(t // 8 + 32, dtype=torch.uint64, device=pool.device)
+            w.run(tables, self.scratch[b.stream], stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        # the wave (host staging), tables and outputs live until the event completes
+        return (ev, w, tables, outs)
+
+    def poll(self, handle) -> bool:
+        return handle[0].query()
+
+    def abandon(self, b: Batch):
+        self._abandoned = getattr(self, "_abandoned", [])
+        self._abandoned.append(b.handle)
+
+    def finish(self, b: Batch):
+        if self.keep_results:
+            for r, o in zip(b.reqs, b.handle[3]):
+                self.results[r.rid] = o.data
+        b.handle[1].close()
         b.handle = None
 
 
@@ -481,10 +587,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--seconds", type=float, default=30.0)
-    ap.add_argument("--streams", type=int, default=8)
-    ap.add_argument("--max-batch", type=int, default=8)
+    ap.add_argument("--streams", type=int, default=None, help="default: 4 for waves, 8 for groups")
+    ap.add_argument("--max-batch", type=int, default=None, help="default: 64 for waves, 8 for groups")
     ap.add_argument("--cap-gb", type=float, default=150.0)
-    ap.add_argument("--ws-gb", type=float, default=6.0)
+    ap.add_argument("--ws-gb", type=float, default=None,
+                    help="workspace (scratch) per stream; default: 16 for waves, 6 for groups")
     ap.add_argument("--log-ns", default="14,15,16")
     ap.add_argument("--seed", type=int, default=2026)
     ap.add_argument("--secret-h", type=int, default=0,
@@ -499,7 +606,14 @@ def main():
                          "queue up the opening seconds")
     ap.add_argument("--criterion", default="table2", choices=["table2", "precision"],
                     help="partitions: Table II, or the precision search's (smallest inner tuple degree)")
+    ap.add_argument("--engine", default="waves", choices=["waves", "groups"],
+                    help="waves: cross-shape batches of one ring degree (any k, level, partition); "
+                         "groups: batches of one (N, k, level, partition) shape")
     args = ap.parse_args()
+    waves = args.engine == "waves" and not args.plaintext
+    args.streams = args.streams or (4 if waves else 8)
+    args.max_batch = args.max_batch or (64 if waves else 8)
+    args.ws_gb = args.ws_gb or (16.0 if waves else 6.0)
     parts = None
     if args.criterion == "precision":
         from . import plan_optimize
@@ -514,7 +628,10 @@ def main():
         def make(rate, seconds, seed, lns):
             return plaintext_requests(rate, seconds, seed, lns, k_range=(2, args.k_max), partitions=parts)
     else:
-        be = GpuBackend(contexts, pools, n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)))
+        if args.engine == "waves":
+            be = WaveBackend(contexts, pools, n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)))
+        else:
+            be = GpuBackend(contexts, pools, n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)))
 
         def make(rate, seconds, seed, lns):
             return mixed_requests(rate, seconds, seed, lns, k_range=(2, args.k_max), partitions=parts)
@@ -553,6 +670,7 @@ def main():
                       "completed": len(sched.completed), "wall_s": round(wall, 3),
                       "sustained_ctmults_s": round(len(sched.completed) / wall, 1), "latency": stats,
                       "batches": sched.admitted_batches, "mean_batch": round(len(reqs) / max(1, sched.admitted_batches), 2),
+                      "engine": "plaintext" if args.plaintext else args.engine,
                       "streams": args.streams, "max_batch": args.max_batch, "cap_gb": args.cap_gb,
                       "resident_gb": round(resident / 1e9, 2), "peak_allocated_gb": round(
                           __import__("torch").cuda.max_memory_allocated() / 1e9, 2), **extra}))

@@ -76,3 +76,55 @@ def test_serving_mix_equals_alone(state):
         want = _alone(contexts, pools, r.log_n, r.k, r.level, r.cts)
         got = be.results[r.rid].cpu().numpy()
         assert np.array_equal(got, want), r
+
+
+def test_wave_executor_uneven_batch_equals_alone(state):
+    """The cross-shape executor (waves of any k and level, one CUDA graph):
+    every product equals ckks_mul_k alone, also on a second replay."""
+    import torch
+
+    from paper_2601_15401_gb300.executor import MulRequest, WaveExecutor
+    contexts, pools = state
+    g = np.random.default_rng(8)
+    reqs, srcs = [], {}
+    for i in range(40):
+        k = int(g.integers(2, 7))
+        log_n = int(g.choice([10, 11]))
+        level = int(g.integers(k, 9)) if k > 2 else int(g.integers(2, 9))
+        reqs.append(MulRequest(log_n, k, level, None, i))
+        srcs[i] = tuple(int(x) for x in g.integers(0, 24, size=k))
+    ex = WaveExecutor(contexts, max_wave=16)
+    ex.plan(reqs)
+    for r in reqs:
+        src = pools[r.log_n].view(torch.int64)[list(srcs[r.rid])][:, :, :r.level]
+        ex.input_view(r.rid).view(torch.int64).copy_(src)
+    ex.capture()
+    ex.replay()
+    torch.cuda.synchronize()
+    first = {}
+    for r in reqs:
+        got = ex.output_view(r.rid).cpu().numpy()
+        assert np.array_equal(got, _alone(contexts, pools, r.log_n, r.k, r.level, srcs[r.rid])), r
+        first[r.rid] = got
+    ex.replay()
+    torch.cuda.synchronize()
+    for r in reqs:
+        assert np.array_equal(ex.output_view(r.rid).cpu().numpy(), first[r.rid])
+    assert len(ex.waves) == sum(-(-sum(1 for r in reqs if r.log_n == n) // 16) for n in (10, 11))
+
+
+def test_wave_serving_mix_equals_alone(state):
+    """Continuous batching with cross-shape batches: requests of one ring
+    degree share a batch whatever their k and level; every result equals the
+    product computed alone."""
+    from paper_2601_15401_gb300.serve import Scheduler, WaveBackend, mixed_requests, run_open_loop
+    contexts, pools = state
+    reqs = mixed_requests(400.0, 0.15, 12, log_ns=(10, 11), L=8, pool_size=24, k_range=(2, 6))
+    assert len(reqs) > 20
+    be = WaveBackend(contexts, pools, n_streams=2, ws_bytes=512 << 20, keep_results=True)
+    sched = Scheduler(be, cap_bytes=int(8e9), max_batch=16)
+    run_open_loop(sched, reqs, timeout=120)
+    assert len(sched.completed) == len(reqs)
+    for r in reqs:
+        want = _alone(contexts, pools, r.log_n, r.k, r.level, r.cts)
+        assert np.array_equal(be.results[r.rid].cpu().numpy(), want), r

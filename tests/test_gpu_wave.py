@@ -101,7 +101,7 @@ def test_wave_rerun_and_new_workspace(S_small):
     t2, s2 = w.buffers()
     for it in items:
         it["out"].data.zero_()
-    w.run(t2[32:], s2[64:])  # other buffers (256-byte aligned offsets): the tables are rebuilt
+    w.run(t2[32:], s2[32:])  # other buffers (256-byte aligned offsets): the tables are rebuilt
     other = [host(it["out"].data) for it in items]
     S.ctx.check()
     for a, b, c in zip(first, again, other):

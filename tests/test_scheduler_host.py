@@ -123,3 +123,48 @@ def test_watchdog_fails_a_stuck_batch_and_the_rest_completes():
     assert [r.rid for r in s.failed] == [0] and s.failed[0].error == "timeout"
     assert sorted(r.rid for r in s.completed) == [1, 2, 3, 4, 5]
     assert be.abandoned == 1 and s.healthy_streams() == 1
+
+
+class GroupingBackend(FakeBackend):
+    """Cross-shape batching: requests of one ring degree share a batch; the
+    footprint and the workspace check see the actual requests."""
+
+    @staticmethod
+    def group_key(r):
+        return (r.log_n,)
+
+    def footprint_reqs(self, reqs):
+        return sum(r.level for r in reqs)
+
+    def fits(self, reqs):
+        return sum(r.k for r in reqs) <= 20
+
+
+def test_cross_shape_batches_group_by_ring_degree():
+    be = GroupingBackend()
+    s = Scheduler(be, cap_bytes=10 ** 9, max_batch=16)
+    # mixed k and level at two ring degrees
+    reqs = [Request(i, 14 + (i % 2), 2 + i % 5, 10 + i % 7, (0,), arrival=i * 1e-6) for i in range(12)]
+    for r in reqs:
+        s.submit(r)
+    s.step(0.0)
+    for b in s.running:
+        assert len({r.log_n for r in b.reqs}) == 1
+        assert sum(r.k for r in b.reqs) <= 20
+    assert any(len({(r.k, r.level) for r in b.reqs}) > 1 for b in s.running)
+    # drain
+    for t in range(1, 50):
+        s.step(float(t))
+        if s.idle():
+            break
+    assert sorted(r.rid for r in s.completed) == list(range(12))
+
+
+def test_cross_shape_admission_uses_request_footprints():
+    be = GroupingBackend()
+    s = Scheduler(be, cap_bytes=25, max_batch=16)  # levels 10..16: at most two requests in flight
+    for i in range(5):
+        s.submit(Request(i, 16, 3, 10 + i, (0,), arrival=i * 1e-6))
+    s.step(0.0)
+    assert sum(len(b.reqs) for b in s.running) == 2
+    assert s.in_use <= 25
