@@ -173,7 +173,15 @@ def run_ours(args, rank, world, local_rank):
     ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.uint64, device=dev)
     torch.cuda.synchronize()
     tuned = None
-    if not args.no_tune:
+    if args.tune:
+        # fixed tunables (e.g. to profile the autotuner's choice without
+        # running the autotuner)
+        tuned = {}
+        for kv in args.tune:
+            key, val = kv.split("=")
+            ctx.tune_set(key, int(val))
+            tuned[key] = int(val)
+    elif not args.no_tune:
         from paper_2601_15401_gb300.executor import autotune
         tuned = autotune(ctx, evk, k=8, batch=4)["choice"]
 
@@ -698,6 +706,7 @@ def main():
                     help="streams the e2e leg spreads its copies over (1 measured best: 465 vs 343 with 4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tune", action="append", default=[], help="key=value library tunable (skips the autotuner)")
     ap.add_argument("--streams", type=int, default=1)
     ap.add_argument("--engine", default="batch", choices=["batch", "waves"],
                     help="batch: one batched call per k; waves: the whole step as one cross-shape wave")

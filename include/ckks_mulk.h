@@ -426,6 +426,17 @@ typedef struct {
 int ckks_profile_enable(ckks_context *ctx, int enable);
 int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, uint32_t *n_out);
 
+/* Host-to-device transfer by the GPU's own loads (no counterpart in the
+ * paper; used to move a step's inputs when that beats the copy engines).
+ * ckks_host_device_pointer returns the device address of pinned host
+ * memory (CKKS_EINVAL if `host` is not pinned and mapped).
+ * ckks_pull copies `bytes` (a multiple of 16; both addresses 16-byte
+ * aligned) from src to dst with a grid of `blocks` CTAs on `stream`; either
+ * address may be device memory or mapped pinned host memory. Caller-owned
+ * buffers; asynchronous. */
+int ckks_host_device_pointer(void *host, void **dev);
+int ckks_pull(void *dst, const void *src, size_t bytes, int blocks, void *stream);
+
 /* Integer-arithmetic peaks (measurement support; no counterpart in the
  * paper). ckks_peak_int launches blocks x threads threads (threads a
  * multiple of 32, at most 256) that each run ckks_peak_chains() independent
@@ -436,9 +447,15 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
  *           Harvey's additions and correction)
  *   kind 2  64 x 64 -> 128-bit multiply-accumulate
  *   kind 3  Montgomery product, R = 2^64
+ *   kind 4  16 x 16 transpose of 64-bit values within each half-warp by
+ *           warp shuffles (the exchange between two radix-16 NTT passes)
+ *   kind 5  the same transpose through shared memory
+ * (kinds 4 and 5 run 16 values per thread and count one operation per
+ * value moved: blocks x threads x 16 x iters; q, w, wp are not used)
  * q: odd modulus below 2^62; w, wp: host arrays of ckks_peak_chains() Shoup
  * pairs (w < q). The caller times the launch on `stream` with CUDA events:
- * operations per second = blocks x threads x chains x iters / time.
+ * operations per second = blocks x threads x chains x iters / time
+ * (kinds 0-3).
  * Returns CKKS_EINVAL for bad arguments, CKKS_ECUDA on a launch error. */
 int ckks_peak_chains(void);
 int ckks_peak_int(int kind, uint64_t q, const uint64_t *w, const uint64_t *wp, int blocks, int threads, int iters,

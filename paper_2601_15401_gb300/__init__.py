@@ -561,7 +561,29 @@ class Wave:
             pass
 
 
-PEAK_KINDS = {"shoup": 0, "butterfly": 1, "mac128": 2, "montgomery": 3}
+def host_device_pointer(host_tensor) -> int:
+    """Device address of a pinned host tensor's memory."""
+    d = ctypes.c_void_p()
+    _check(lib().ckks_host_device_pointer(ctypes.c_void_p(host_tensor.data_ptr()), ctypes.byref(d)),
+           "ckks_host_device_pointer")
+    return d.value
+
+
+def pull(dst, src, nbytes: int | None = None, blocks: int = 0, stream=None):
+    """Copy src -> dst (device tensors, or a pinned host tensor on either side)
+    with the GPU's own loads and stores (ckks_pull)."""
+    import torch
+    nbytes = nbytes if nbytes is not None else dst.numel() * dst.element_size()
+
+    def addr(t):
+        return host_device_pointer(t) if not t.is_cuda else t.data_ptr()
+    if not blocks:
+        blocks = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8
+    _check(lib().ckks_pull(ctypes.c_void_p(addr(dst)), ctypes.c_void_p(addr(src)), nbytes, blocks,
+                           _stream(stream)), "ckks_pull")
+
+
+PEAK_KINDS = {"shoup": 0, "butterfly": 1, "mac128": 2, "montgomery": 3, "transpose_shfl": 4, "transpose_smem": 5}
 
 
 def peak_int(kind: str, q: int, blocks: int, threads: int = 256, iters: int = 4096, reps: int = 5,
@@ -588,7 +610,8 @@ def peak_int(kind: str, q: int, blocks: int, threads: int = 256, iters: int = 40
         ms = e0.elapsed_time(e1)
         if r and (best is None or ms < best):
             best = ms
-    return blocks * threads * chains * iters / (best / 1e3)
+    per_thread = 16 if PEAK_KINDS[kind] >= 4 else chains
+    return blocks * threads * per_thread * iters / (best / 1e3)
 
 
 def plan_optimize(k: int, criterion: str = "rs_units", level: int = 0, K: int = 0, alpha: int = 0):

@@ -82,6 +82,8 @@ SIGNATURES = {
     "ckks_tune_get": [V, ctypes.c_char_p, V],
     "ckks_strerror": [I],
     "ckks_peak_chains": [],
+    "ckks_host_device_pointer": [V, V],
+    "ckks_pull": [V, V, SZ, I, V],
     "ckks_wave_create": [V, V, U32, V, V],
     "ckks_wave_workspace_size": [V, V, V],
     "ckks_wave_run": [V, V, SZ, V, SZ, V],

@@ -136,7 +136,14 @@ template <int MAXT>
 __global__ void __launch_bounds__(kThreads) tensor_table_kernel(const TensorJob *jobs, int N, int log_n,
                                                                 const ModQ *mods, const u64 *rpow) {
     __shared__ TensorJob J;
-    if (threadIdx.x == 0) J = jobs[blockIdx.y];
+    {
+        // the entry is copied by many threads, one word each
+        static_assert(sizeof(TensorJob) % sizeof(u64) == 0, "TensorJob is a whole number of words");
+        constexpr int W = sizeof(TensorJob) / sizeof(u64);
+        const u64 *src = reinterpret_cast<const u64 *>(jobs + blockIdx.y);
+        u64 *dst = reinterpret_cast<u64 *>(&J);
+        for (int i = threadIdx.x; i < W; i += blockDim.x) dst[i] = src[i];
+    }
     __syncthreads();
     const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (i64)J.level * N) return;

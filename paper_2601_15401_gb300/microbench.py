@@ -34,7 +34,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", choices=["ntt", "mul_k", "mul2", "chain3", "rotate", "encode", "decode", "precision",
-                                         "peak", "tensor_rates"], default="ntt")
+                                         "peak", "tensor_rates", "h2d"], default="ntt")
     ap.add_argument("--log-n", type=int, default=16)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--k", type=int, default=8)
@@ -59,6 +59,8 @@ def main():
         return peak(args)
     if args.op == "tensor_rates":
         return tensor_rates(args)
+    if args.op == "h2d":
+        return h2d(args)
     if args.params == "small":
         p = synth.params_small(log_n=args.log_n)
     elif args.params == "mid":
@@ -207,6 +209,40 @@ def main():
                         "Gops": round(v["int_ops"] / (v["total_ms"] / 1e3) / 1e9, 2)} for n, v in prof.items()}}))
 
 
+def h2d(args):
+    """Host-to-device bandwidth from pinned memory: the copy engines
+    (cudaMemcpyAsync through torch) against the GPU's own loads (ckks_pull
+    over the mapped host memory), 4 GiB, best and first of several passes."""
+    import torch
+
+    import paper_2601_15401_gb300 as G
+    nbytes = 4 << 30
+    host = torch.empty(nbytes // 8, dtype=torch.int64, pin_memory=True)
+    host.copy_(torch.arange(nbytes // 8, dtype=torch.int64))
+    dev = torch.empty(nbytes // 8, dtype=torch.int64, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    res = {"op": "h2d", "bytes": nbytes}
+
+    def rate(fn, reps=5):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            out.append(round(nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
+        return out
+    res["copy_engine_GBps"] = rate(lambda: dev.copy_(host, non_blocking=True))
+    for per_sm in (2, 8, 32):
+        dev.zero_()
+        res[f"pull_{per_sm}_per_sm_GBps"] = rate(lambda: G.pull(dev, host, blocks=sms * per_sm))
+        res[f"pull_{per_sm}_per_sm_equal"] = bool(torch.equal(dev.cpu(), host))
+    res["device_to_host_copy_engine_GBps"] = rate(lambda: host.copy_(dev, non_blocking=True))
+    print(json.dumps(res))
+
+
 def tensor_rates(args):
     """Dense tensor-core rates of this GPU through the vendor GEMMs (context
     for the BConv-as-GEMM question: an exact byte-split BConv would run as
@@ -251,6 +287,8 @@ def peak(args):
     for bits in (50, 60):
         q = synth.prime_chain(bits, 1)[0]
         for kind in G.PEAK_KINDS:
+            if kind.startswith("transpose") and bits == 60:
+                continue
             best = 0.0
             for per_sm in (1, 2, 4, 8, 16):
                 r = G.peak_int(kind, q, blocks=sms * per_sm, threads=256, iters=2048)
