@@ -535,6 +535,19 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     down = torch.cuda.Stream(device=dev)
     used = {}  # k -> event: the last multiply that read dev_inp[k]
 
+    import paper_2601_15401_gb300 as G
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def upload(k, b, cs):
+        """One batch element's inputs host -> device on stream cs: by the GPU's
+        own loads over the host link (ckks_pull, the default: the copy engines
+        restart at a fraction of the link's rate after device compute), or by
+        the copy engines (cudaMemcpyAsync)."""
+        if args.h2d == "pull":
+            G.pull(dev_inp[k][b], host_in[b, :k], blocks=sms * args.pull_ctas_per_sm, stream=cs)
+        else:
+            dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
+
     def step():
         up = {}
         for k in ks:
@@ -544,7 +557,7 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
                     cs.wait_event(used[k])
                 with torch.cuda.stream(cs):
                     for b in range(c, B, len(copies)):
-                        dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
+                        upload(k, b, cs)
                     e = torch.cuda.Event()
                     e.record(cs)
                     evs.append(e)
@@ -574,7 +587,7 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
             with torch.cuda.stream(cs):
                 for k in ks:
                     for b in range(c, B, len(copies)):
-                        dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
+                        upload(k, b, cs)
         for cs in copies[1:]:
             ev = torch.cuda.Event()
             ev.record(cs)
@@ -612,6 +625,8 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
             "h2d_GBps_alone": [round(bw_before, 1), round(bw_after, 1)],
             "h2d_GBps_warmup": [round(x, 1) for x in warm_bw],
             "copy_streams": len(copies), "host_numa": numa_note,
+            "h2d": "GPU loads over the host link (ckks_pull, %d CTAs)" % (sms * args.pull_ctas_per_sm)
+                   if args.h2d == "pull" else "copy engines (cudaMemcpyAsync)",
             "overlap": "uploads (own stream) overlap the multiplies of this and the previous step; downloads on "
                        "a second stream"}
 
@@ -702,6 +717,9 @@ def main():
     ap.add_argument("--ks", default="")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--h2d", default="pull", choices=["pull", "copy"],
+                    help="e2e uploads: GPU loads over the host link (pull) or the copy engines (copy)")
+    ap.add_argument("--pull-ctas-per-sm", type=int, default=1)
     ap.add_argument("--copy-streams", type=int, default=1,
                     help="streams the e2e leg spreads its copies over (1 measured best: 465 vs 343 with 4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -52,6 +52,7 @@ def main():
     ap.add_argument("--scale-bits", type=int, default=50, help="--op precision: log2 of the encoding scale")
     ap.add_argument("--criterion", default="table2", choices=["table2", "precision"],
                     help="--op precision: Table II partitions or the precision search's")
+    ap.add_argument("--seconds-compute", type=float, default=3.0, help="--op h2d: device work between probes")
     args = ap.parse_args()
     if args.op == "precision":
         return precision(args)
@@ -210,20 +211,26 @@ def main():
 
 
 def h2d(args):
-    """Host-to-device bandwidth from pinned memory: the copy engines
+    """Host-to-device bandwidth from pinned memory, 4 GiB: the copy engines
     (cudaMemcpyAsync through torch) against the GPU's own loads (ckks_pull
-    over the mapped host memory), 4 GiB, best and first of several passes."""
+    over the mapped host memory); then the same after device-to-host traffic
+    into a second pinned buffer and after seconds of device compute (the
+    state a benchmark step leaves behind), and for host memory backed by
+    transparent huge pages and registered with the driver."""
+    import mmap
+
     import torch
 
     import paper_2601_15401_gb300 as G
     nbytes = 4 << 30
-    host = torch.empty(nbytes // 8, dtype=torch.int64, pin_memory=True)
-    host.copy_(torch.arange(nbytes // 8, dtype=torch.int64))
-    dev = torch.empty(nbytes // 8, dtype=torch.int64, device="cuda")
+    words = nbytes // 8
+    host = torch.empty(words, dtype=torch.int64, pin_memory=True)
+    host.copy_(torch.arange(words, dtype=torch.int64))
+    dev = torch.empty(words, dtype=torch.int64, device="cuda")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     res = {"op": "h2d", "bytes": nbytes}
 
-    def rate(fn, reps=5):
+    def rate(fn, n=nbytes, reps=3):
         out = []
         for _ in range(reps):
             torch.cuda.synchronize()
@@ -232,14 +239,45 @@ def h2d(args):
             fn()
             e1.record()
             e1.synchronize()
-            out.append(round(nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
+            out.append(round(n / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
         return out
-    res["copy_engine_GBps"] = rate(lambda: dev.copy_(host, non_blocking=True))
-    for per_sm in (2, 8, 32):
-        dev.zero_()
-        res[f"pull_{per_sm}_per_sm_GBps"] = rate(lambda: G.pull(dev, host, blocks=sms * per_sm))
-        res[f"pull_{per_sm}_per_sm_equal"] = bool(torch.equal(dev.cpu(), host))
-    res["device_to_host_copy_engine_GBps"] = rate(lambda: host.copy_(dev, non_blocking=True))
+
+    def probe(tag, src):
+        res[f"{tag}/copy_engine_GBps"] = rate(lambda: dev.copy_(src, non_blocking=True))
+        try:
+            G.host_device_pointer(src)
+        except G.CkksError:
+            res[f"{tag}/pull_GBps"] = "host memory not mapped"
+            return
+        res[f"{tag}/pull_GBps"] = rate(lambda: G.pull(dev, src, blocks=sms * 8))
+
+    probe("fresh", host)
+    # device-to-host traffic into another pinned buffer
+    back = torch.empty(words // 2, dtype=torch.int64, pin_memory=True)
+    res["d2h_GBps"] = rate(lambda: back.copy_(dev[:words // 2], non_blocking=True), n=nbytes // 2)
+    probe("after_d2h", host)
+    # seconds of device work over 24 GiB of HBM
+    big = torch.empty(3 * words, dtype=torch.int64, device="cuda")
+    t_end = __import__("time").time() + args.seconds_compute
+    while __import__("time").time() < t_end:
+        big.add_(1)
+        torch.cuda.synchronize()
+    del big
+    probe("after_compute", host)
+    # transparent-huge-page host memory registered with the driver
+    mm = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+    try:
+        mm.madvise(mmap.MADV_HUGEPAGE)
+        res["thp"] = True
+    except (AttributeError, OSError):
+        res["thp"] = False
+    thp = torch.frombuffer(mm, dtype=torch.int64)
+    thp.copy_(host)
+    rc = torch.cuda.cudart().cudaHostRegister(thp.data_ptr(), nbytes, 0)
+    res["register_rc"] = int(rc.value if hasattr(rc, "value") else rc)
+    if res["register_rc"] == 0:
+        probe("thp_registered", thp)
+        torch.cuda.cudart().cudaHostUnregister(thp.data_ptr())
     print(json.dumps(res))
 
 
