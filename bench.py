@@ -625,7 +625,7 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
             "h2d_GBps_alone": [round(bw_before, 1), round(bw_after, 1)],
             "h2d_GBps_warmup": [round(x, 1) for x in warm_bw],
             "copy_streams": len(copies), "host_numa": numa_note,
-            "h2d": "GPU loads over the host link (ckks_pull, %d CTAs)" % (sms * args.pull_ctas_per_sm)
+            "h2d": "GPU loads over the host link (ckks_pull, %d CTAs of 64 threads)" % (sms * args.pull_ctas_per_sm)
                    if args.h2d == "pull" else "copy engines (cudaMemcpyAsync)",
             "overlap": "uploads (own stream) overlap the multiplies of this and the previous step; downloads on "
                        "a second stream"}
@@ -719,7 +719,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--h2d", default="pull", choices=["pull", "copy"],
                     help="e2e uploads: GPU loads over the host link (pull) or the copy engines (copy)")
-    ap.add_argument("--pull-ctas-per-sm", type=int, default=1)
+    ap.add_argument("--pull-ctas-per-sm", type=int, default=1, help="64-thread CTAs per SM of the e2e uploads")
     ap.add_argument("--copy-streams", type=int, default=1,
                     help="streams the e2e leg spreads its copies over (1 measured best: 465 vs 343 with 4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -431,7 +431,8 @@ int ckks_profile_read(ckks_context *ctx, ckks_kernel_stats *out, uint32_t max, u
  * ckks_host_device_pointer returns the device address of pinned host
  * memory (CKKS_EINVAL if `host` is not pinned and mapped).
  * ckks_pull copies `bytes` (a multiple of 16; both addresses 16-byte
- * aligned) from src to dst with a grid of `blocks` CTAs on `stream`; either
+ * aligned) from src to dst with a grid of `blocks` CTAs of 64 threads on
+ * `stream`; either
  * address may be device memory or mapped pinned host memory. Caller-owned
  * buffers; asynchronous. */
 int ckks_host_device_pointer(void *host, void **dev);
@@ -467,10 +468,7 @@ int ckks_peak_int(int kind, uint64_t q, const uint64_t *w, const uint64_t *wp, i
  * reading it gives the column value) (1024..8192,
  * power of two; default 4096), "bconv_threads" = threads per BConv block
  * (64..1024, multiple of 32; default 256), "mac_threads" = threads per
- * key-MAC block (same range), "ntt_pipe" = 1 (default) lets phases with
- * plain loads of 16-byte aligned limbs run as persistent CTAs that copy the
- * next tile into shared memory (cp.async) while transforming the current
- * one, 0 = one CTA per tile.
+ * key-MAC block (same range).
  * Forms of the rescaling, for measuring the paper's reformulations (every
  * rescaling form gives the same residues): "inner_rescale" 0 = Algorithm 1 (mu INTT
  * + (l - mu) NTT per polynomial, default), 1 = mu single rescales of Eq. 7,

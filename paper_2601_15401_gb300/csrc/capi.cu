@@ -713,7 +713,6 @@ static int *tune_slot(ckks_context *ctx, const char *key, int &lo, int &hi) {
     if (!strcmp(key, "ntt_tile_blocks")) { lo = 1024; hi = 8192; return &ctx->c.tune_ntt_tile_blocks; }
     if (!strcmp(key, "bconv_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_bconv_threads; }
     if (!strcmp(key, "mac_threads")) { lo = 64; hi = 1024; return &ctx->c.tune_mac_threads; }
-    if (!strcmp(key, "ntt_pipe")) { lo = 0; hi = 1; return &ctx->c.tune_ntt_pipe; }
     if (!strcmp(key, "inner_rescale")) { lo = 0; hi = 2; return &ctx->c.tune_inner_rescale; }
     if (!strcmp(key, "root_rescale")) { lo = 0; hi = 1; return &ctx->c.tune_root_rescale; }
     if (!strcmp(key, "moddown")) { lo = 0; hi = 1; return &ctx->c.tune_moddown; }

@@ -143,7 +143,6 @@ struct Context {
     int tune_ntt_tile_blocks = 4096;  // elements per CTA tile, block phases
     int tune_bconv_threads = 256;
     int tune_mac_threads = 256;
-    int tune_ntt_pipe = 1;            // 1: plain-load phases take the pipelined persistent kernel
     // forms of the rescaling (same results; for measuring the paper's
     // reformulations): see multi_rs and run_mul_k in engine.cu
     int tune_inner_rescale = 0;
@@ -187,11 +186,9 @@ inline void count_kernel(const Context &C) { count_op(C, OP_KERNELS, 1); }
 void ntt_geometry(int logN, int &log_n1, int &log_n2);
 // phase launch over a device table of NttJob (ntt_launch.cu); jobs: device
 // array of n_jobs entries
-// aligned16: every entry's input limb starts on a 16-byte boundary (lets
-// plain-load phases take the pipelined kernel)
 cudaError_t launch_ntt_phase_table(const Context &C, bool fwd, bool cols, const NttJob *jobs, int n_jobs,
                                    const LoadSpec &L, const StoreSpec &S, double alg_bytes, double ops,
-                                   bool aligned16, cudaStream_t st);
+                                   cudaStream_t st);
 cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJobs &J, const LoadSpec &L,
                              const StoreSpec &S, cudaStream_t st);
 cudaError_t ntt_transform(const Context &C, bool fwd, const LimbJobs &J, const LoadSpec &L, const StoreSpec &S,

@@ -82,10 +82,6 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
     if (S.mode == ST_SCALE || S.mode == ST_MODDOWN || S.mode == ST_MRS) ops += jobs_d * (double)C.N;
     ProfScope ps(C, fwd ? (cols ? KC_NTT_FWD_COLS : KC_NTT_FWD_BLOCKS) : (cols ? KC_NTT_INV_COLS : KC_NTT_INV_BLOCKS),
                  bytes, st, ops);
-    // the pipelined kernel copies column rows in 16-byte pieces: every limb of
-    // the view must start on a 16-byte boundary
-    G.pipe = C.tune_ntt_pipe && L.mode == LD_PLAIN && L.a.ptr && (size_t)L.a.ptr % 16 == 0 &&
-             L.a.bstride % 2 == 0 && L.a.pstride % 2 == 0 && C.N % 2 == 0;
     return fwd ? ntt_dispatch_uniform_fwd(cols, logn, P, J, L, S, G)
                : ntt_dispatch_uniform_inv(cols, logn, P, J, L, S, G);
 }
@@ -95,7 +91,7 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
 // table's entries).
 cudaError_t launch_ntt_phase_table(const Context &C, bool fwd, bool cols, const NttJob *jobs, int n_jobs,
                                    const LoadSpec &L, const StoreSpec &S, double alg_bytes, double ops,
-                                   bool aligned16, cudaStream_t st) {
+                                   cudaStream_t st) {
     if (n_jobs <= 0) return cudaSuccess;
     NttPhase P;
     PhaseLaunch G;
@@ -105,7 +101,6 @@ cudaError_t launch_ntt_phase_table(const Context &C, bool fwd, bool cols, const 
     count_kernel(C);
     ProfScope ps(C, fwd ? (cols ? KC_NTT_FWD_COLS : KC_NTT_FWD_BLOCKS) : (cols ? KC_NTT_INV_COLS : KC_NTT_INV_BLOCKS),
                  alg_bytes, st, ops);
-    G.pipe = C.tune_ntt_pipe && L.mode == LD_PLAIN && aligned16;
     return fwd ? ntt_dispatch_table_fwd(cols, logn, P, jobs, n_jobs, L, S, G)
                : ntt_dispatch_table_inv(cols, logn, P, jobs, n_jobs, L, S, G);
 }

@@ -40,8 +40,6 @@
 // (LimbJobs), or from a device table of NttJob entries (limbs of different
 // products, levels and tree nodes in one launch).
 #pragma once
-#include <algorithm>
-
 #include "common.cuh"
 #include "internal.h"
 
@@ -341,7 +339,7 @@ struct PassAccess {
     static constexpr bool direct_in = direct && CKKS_NTT_DIRECT_IN;
 };
 
-template <int LOGN, bool FWD, bool COLS, int LM, int SM, bool PRE, int I>
+template <int LOGN, bool FWD, bool COLS, int LM, int SM, int I>
 __device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS, LOGN> &lay, const ulonglong2 *tw, int tw_b0,
                                            int tw_bmul, u64 q, const LoadCtx &lc, const StoreCtx &sc, int t0,
                                            int log_n2) {
@@ -349,19 +347,17 @@ __device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS, LOGN> &la
     if constexpr (I < NP) {
         constexpr int PP = FWD ? I : NP - 1 - I;
         constexpr bool first = I == 0, last = I == NP - 1;
-        constexpr bool gin = first && PassAccess<LOGN, COLS, PP>::direct_in && !PRE;
+        constexpr bool gin = first && PassAccess<LOGN, COLS, PP>::direct_in;
         constexpr bool gout = last && PassAccess<LOGN, COLS, PP>::direct;
         run_pass<LOGN, Pass<LOGN, PP>::len, Pass<LOGN, PP>::start, FWD, COLS, gin, gout, LM, SM>(
             sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
         if (!last || !gout) __syncthreads();
-        run_passes<LOGN, FWD, COLS, LM, SM, PRE, I + 1>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
+        run_passes<LOGN, FWD, COLS, LM, SM, I + 1>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
     }
 }
 
-// One tile (CTA) of one limb: tile index `tile` of the phase. PRE: the
-// tile's input is already in shared memory (copied ahead by the pipelined
-// kernel), so no pass reads global memory.
-template <int LOGN, bool FWD, bool COLS, int LM, int SM, bool PRE = false>
+// One tile (CTA) of one limb: tile index `tile` of the phase.
+template <int LOGN, bool FWD, bool COLS, int LM, int SM>
 __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulonglong2 *tw, u64 q,
                                            const LoadCtx &lc, const StoreCtx &sc, int tile) {
     constexpr int n = 1 << LOGN;
@@ -372,7 +368,7 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
     const int t0 = tile << lsub;  // first column (COLS) or block (!COLS)
     constexpr int PF = FWD ? 0 : NP - 1;
     constexpr int PL = FWD ? NP - 1 : 0;
-    constexpr bool gin = PassAccess<LOGN, COLS, PF>::direct_in || PRE;
+    constexpr bool gin = PassAccess<LOGN, COLS, PF>::direct_in;
     constexpr bool gout = PassAccess<LOGN, COLS, PL>::direct;
     const int total = n_sub << LOGN;
     // twiddle base: columns -> 1; blocks -> N1 + block
@@ -407,7 +403,7 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
         }
         __syncthreads();
     }
-    run_passes<LOGN, FWD, COLS, LM, SM, PRE, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
+    run_passes<LOGN, FWD, COLS, LM, SM, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
     if (!gout) {
         // shared -> global with the fused store (coalesced)
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -451,117 +447,12 @@ __global__ void __launch_bounds__(256, MINB) ntt_phase_table_kernel(NttPhase P, 
 }
 
 // ---------------------------------------------------------------------------
-// pipelined phase kernel (plain loads): persistent CTAs walk the phase's
-// (limb, tile) items; while one item's passes run on one shared-memory
-// buffer, the next item's input streams into the other with cp.async, so
-// the global-load latency of a tile is hidden behind the previous tile's
-// butterflies instead of stalling every tile's first pass.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async8(u64 *dst, const u64 *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(u64 *dst, const u64 *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Copies tile `tile` of the limb at `a` into shared memory (the tile's
-// layout), asynchronously. Column rows of n_sub >= 2 words move in 16-byte
-// pieces (rows start on 16-byte boundaries); block rows, padded every 16
-// words, in 8-byte pieces.
-template <int LOGN, bool COLS>
-__device__ __forceinline__ void issue_tile(u64 *buf, const u64 *a, const NttPhase &P, int tile) {
-    constexpr int n = 1 << LOGN;
-    const int lsub = P.log_sub;
-    const int n_sub = 1 << lsub;
-    const int t0 = tile << lsub;
-    Layout<COLS, LOGN> lay{lsub};
-    if (COLS && n_sub >= 2) {
-        const int half = n_sub >> 1;  // 16-byte pieces per row
-        const int pieces = half << LOGN;
-        for (int idx = threadIdx.x; idx < pieces; idx += blockDim.x) {
-            const int k = idx / half, c = (idx - k * half) << 1;
-            cp_async16(buf + (k << lsub) + c, a + t0 + c + ((i64)k << P.log_n2));
-        }
-    } else {
-        const int total = n_sub << LOGN;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int sp, k;
-            i64 e;
-            if (COLS) { k = idx >> lsub; sp = idx & (n_sub - 1); e = t0 + sp + ((i64)k << P.log_n2); }
-            else { sp = idx >> LOGN; k = idx & (n - 1); e = ((i64)(t0 + sp) << LOGN) + k; }
-            cp_async8(buf + lay.off(sp, k), a + e);
-        }
-    }
-}
-
-// Input limb of item `job` (plain load: the limb's own pointer).
-__device__ __forceinline__ const u64 *item_src(const LimbJobs &J, const LoadSpec &L, int N, int job) {
-    int b, p, l;
-    decode_job(J, job, b, p, l);
-    return limb_ptr(L.a, b, p, J.slot[l], N);
-}
-
-template <int LOGN, bool FWD, bool COLS, int SM, int MINB, bool TABLE>
-__global__ void __launch_bounds__(256, MINB) ntt_phase_pipe_kernel(NttPhase P, LimbJobs J, const NttJob *jobs,
-                                                                   int tiles, int n_items, int buf_words, LoadSpec L,
-                                                                   StoreSpec S) {
-    extern __shared__ u64 sm[];
-    u64 *buf[2] = {sm, sm + buf_words};
-    int item = blockIdx.x;
-    if (item >= n_items) return;
-    {
-        const int job = item / tiles;
-        issue_tile<LOGN, COLS>(buf[0], TABLE ? jobs[job].a : item_src(J, L, P.N, job), P, item - job * tiles);
-        cp_async_commit();
-    }
-    for (int i = 0; item < n_items; ++i, item += gridDim.x) {
-        const int next = item + gridDim.x;
-        if (next < n_items) {
-            const int job = next / tiles;
-            issue_tile<LOGN, COLS>(buf[(i + 1) & 1], TABLE ? jobs[job].a : item_src(J, L, P.N, job), P,
-                                   next - job * tiles);
-        }
-        cp_async_commit();      // possibly empty: keeps one group per item
-        cp_async_wait_prior();  // this item's copies (all but the newest group) have landed
-        __syncthreads();
-        const int job = item / tiles;
-        const int tile = item - job * tiles;
-        int prime;
-        LoadCtx lc;
-        StoreCtx sc;
-        ModQ m;
-        if constexpr (TABLE) {
-            const NttJob j = jobs[job];
-            prime = j.prime;
-            m = P.mods[prime];
-            lc = make_load(L, j, P.N, m);
-            sc = make_store(S, j, P.N, m);
-        } else {
-            int b, p, l;
-            decode_job(J, job, b, p, l);
-            prime = J.prime[l];
-            m = P.mods[prime];
-            lc = make_load(L, J, P.N, b, p, l, prime, m);
-            sc = make_store(S, J, P.N, b, p, l, prime, m);
-        }
-        const ulonglong2 *tw = (FWD ? P.tw_fwd : P.tw_inv) + (i64)prime * P.N;
-        phase_tile<LOGN, FWD, COLS, LD_PLAIN, SM, true>(buf[i & 1], P, tw, m.q, lc, sc, tile);
-        __syncthreads();  // every thread is done with this buffer before it is refilled
-    }
-}
-
-// ---------------------------------------------------------------------------
 // host-side launch of one instantiation
 // ---------------------------------------------------------------------------
 struct PhaseLaunch {
     int tiles, threads;
     size_t smem;
     cudaStream_t st;
-    bool pipe = false;  // plain loads may take the pipelined kernel (16-byte aligned limbs)
 };
 
 #ifndef CKKS_NTT_MINB
@@ -601,29 +492,6 @@ static inline cudaError_t launch_table(const NttPhase &P, const NttJob *jobs, in
     return cudaGetLastError();
 }
 
-// Persistent launch of the pipelined kernel: as many CTAs as fit the GPU at
-// once (at most one per item), two tile buffers each.
-template <int LOGN, bool FWD, bool COLS, int SM, int MINB, bool TABLE>
-static inline cudaError_t launch_pipe(const NttPhase &P, const LimbJobs *J, const NttJob *jobs, int n_jobs,
-                                      const LoadSpec &L, const StoreSpec &S, const PhaseLaunch &G) {
-    auto kern = ntt_phase_pipe_kernel<LOGN, FWD, COLS, SM, MINB, TABLE>;
-    const int buf_words = (int)((G.smem / sizeof(u64) + 1) & ~(size_t)1);
-    const size_t smem = 2 * (size_t)buf_words * sizeof(u64);
-    cudaError_t e = allow_smem(kern, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G.threads, smem)) != cudaSuccess) return e;
-    const long long items = (long long)(TABLE ? n_jobs : J->n_batch * J->n_polys * J->n_limbs) * G.tiles;
-    if (items <= 0) return cudaSuccess;
-    if (items > 0x7FFFFFFFll || per_sm < 1) return cudaErrorInvalidValue;
-    const long long grid = std::min<long long>(items, (long long)per_sm * sms);
-    LimbJobs none{};
-    kern<<<(unsigned)grid, G.threads, smem, G.st>>>(P, J ? *J : none, jobs, G.tiles, (int)items, buf_words, L, S);
-    return cudaGetLastError();
-}
-
 // Dispatch of one direction (FWD) and job source (TABLE) over the phase
 // geometry (cols, log2 n) and the modes: a specialised kernel for the mode
 // combinations of the hot path at n = 128 / 256 (N = 2^14 .. 2^16), the
@@ -632,10 +500,6 @@ template <bool FWD, bool TABLE>
 static inline cudaError_t dispatch_phase(bool cols, int logn, const NttPhase &P, const LimbJobs *J,
                                          const NttJob *jobs, int n_jobs, const LoadSpec &L, const StoreSpec &S,
                                          const PhaseLaunch &G) {
-#define CKKS_PIPE(LG, CO, SMv, MB)                                                         \
-    do {                                                                                   \
-        if (G.pipe) return launch_pipe<LG, FWD, CO, SMv, MB, TABLE>(P, J, jobs, n_jobs, L, S, G); \
-    } while (0)
 #define CKKS_LAUNCH(LG, CO, LMv, SMv, MB)                                                  \
     do {                                                                                   \
         if constexpr (TABLE) return launch_table<LG, FWD, CO, LMv, SMv, MB>(P, jobs, n_jobs, L, S, G); \
@@ -646,26 +510,20 @@ static inline cudaError_t dispatch_phase(bool cols, int logn, const NttPhase &P,
     if (logn == LG) {                                                                              \
         if constexpr (FWD) {                                                                       \
             if (cols && S.mode == ST_LAZY) {                                                       \
-                if (L.mode == LD_PLAIN) CKKS_PIPE(LG, true, ST_LAZY, CKKS_NTT_FAST_MINB);            \
                 if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB); \
                 if (L.mode == LD_EQ17) CKKS_LAUNCH(LG, true, LD_EQ17, ST_LAZY, CKKS_NTT_MINB);        \
             }                                                                                      \
             if (!cols && L.mode == LD_PLAIN) {                                                     \
-                if (S.mode == ST_REDUCE) CKKS_PIPE(LG, false, ST_REDUCE, CKKS_NTT_FAST_MINB);         \
                 if (S.mode == ST_REDUCE) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_REDUCE, CKKS_NTT_FAST_MINB); \
-                if (S.mode == ST_MRS) CKKS_PIPE(LG, false, ST_MRS, CKKS_NTT_FAST_MINB);               \
                 if (S.mode == ST_MRS) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_MRS, CKKS_NTT_FAST_MINB);   \
             }                                                                                      \
         } else {                                                                                   \
             if (!cols && S.mode == ST_LAZY) {                                                      \
-                if (L.mode == LD_PLAIN) CKKS_PIPE(LG, false, ST_LAZY, CKKS_NTT_FAST_MINB);           \
                 if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB); \
                 if (L.mode == LD_ADD) CKKS_LAUNCH(LG, false, LD_ADD, ST_LAZY, CKKS_NTT_FAST_MINB);    \
             }                                                                                      \
             if (cols && L.mode == LD_PLAIN) {                                                      \
-                if (S.mode == ST_SCALE) CKKS_PIPE(LG, true, ST_SCALE, CKKS_NTT_FAST_MINB);            \
                 if (S.mode == ST_SCALE) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_SCALE, CKKS_NTT_FAST_MINB); \
-                if (S.mode == ST_MODDOWN) CKKS_PIPE(LG, true, ST_MODDOWN, CKKS_NTT_FAST_MINB);        \
                 if (S.mode == ST_MODDOWN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_MODDOWN, CKKS_NTT_FAST_MINB); \
             }                                                                                      \
         }                                                                                          \
@@ -691,7 +549,6 @@ static inline cudaError_t dispatch_phase(bool cols, int logn, const NttPhase &P,
 #undef CKKS_GENERIC
 #undef CKKS_FAST
 #undef CKKS_LAUNCH
-#undef CKKS_PIPE
 }
 
 // ntt_uf.cu / ntt_ui.cu / ntt_tf.cu / ntt_ti.cu

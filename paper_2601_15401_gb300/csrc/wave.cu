@@ -66,7 +66,6 @@ struct Stage {
     std::vector<MacJob> mac;
     std::vector<MacTarget> targets;
     size_t off = 0, off2 = 0;  // byte offsets of the table(s)
-    bool aligned16 = true;     // every NTT entry's input limb on a 16-byte boundary
     double bytes = 0, ops = 0;
     unsigned long long limb_transforms = 0;
     int count() const {
@@ -139,7 +138,6 @@ struct Builder {
         a.L = L1;
         a.S = S1;
         a.ntt.push_back(p1);
-        a.aligned16 = a.aligned16 && (size_t)p1.a % 16 == 0;
         a.bytes += bytes1;
         a.ops += ops1;
         a.limb_transforms += 1;
@@ -149,7 +147,6 @@ struct Builder {
         b.L = L2;
         b.S = S2;
         b.ntt.push_back(p2);
-        b.aligned16 = b.aligned16 && (size_t)p2.a % 16 == 0;
         b.bytes += bytes2;
         b.ops += ops2;
     }
@@ -473,7 +470,7 @@ cudaError_t enqueue(ckks_wave &W, char *ws /* the job tables */, cudaStream_t st
         case SK_NTT:
             if (s.fwd == s.cols) count_op(C, s.fwd ? OP_LIMB_NTT : OP_LIMB_INTT, s.limb_transforms);
             e = launch_ntt_phase_table(C, s.fwd, s.cols, (const NttJob *)(ws + s.off), n, s.L, s.S, s.bytes, s.ops,
-                                       s.aligned16, st);
+                                       st);
             break;
         case SK_TENSOR:
             e = launch_tensor_table(C, (const TensorJob *)(ws + s.off), n, s.maxt, s.max_level, s.bytes, st);

@@ -271,12 +271,10 @@ TUNE_SPACE = {
     "ntt_tile_blocks": [1024, 2048, 4096],
     "bconv_threads": [128, 256, 512],
     "mac_threads": [128, 256, 512],
-    "ntt_pipe": [0, 1],
 }
 # the library's defaults (Context in csrc/internal.h): the reference every
 # candidate's output is compared with
-TUNE_DEFAULTS = {"ntt_tile_cols": 4096, "ntt_tile_blocks": 4096, "bconv_threads": 256, "mac_threads": 256,
-                 "ntt_pipe": 1}
+TUNE_DEFAULTS = {"ntt_tile_cols": 4096, "ntt_tile_blocks": 4096, "bconv_threads": 256, "mac_threads": 256}
 
 
 def _cache_path() -> str:
