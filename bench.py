@@ -308,10 +308,10 @@ def run_ours(args, rank, world, local_rank):
                             "frac": round(achieved_gbs / hbm_peak, 4),
                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"},
                     "fmaheavy_busy": busy,
-                    "limiter": "integer multiply (fmaheavy) pipe, not HBM: ncu shows it 54-75 % busy in the NTT "
-                               "phases with math-pipe throttle the top stall, about 14 of its instructions per "
-                               "64-bit Shoup product, DRAM at 23-28 % and traffic equal to the algorithmic bytes "
-                               "(profiles/ntt_phase_pipes_N65536_batch8.md, ntt_phase_N65536_batch16.md)"}
+                    "limiter": "integer multiply (fmaheavy) pipe, not HBM: ncu shows it 64-73 % busy in the NTT "
+                               "phases (95 % in the register-only butterfly stream the peak comes from), 62-66 of its "
+                               "instructions per element for 4 butterflies, DRAM at 26 % of peak and traffic at most "
+                               "the algorithmic bytes (profiles/ntt_phase_N65536_batch8.md, int_peaks_gb300.md)"}
     def int_frac(n, v):
         pk = int_peaks.get(op_unit(n))
         return round(v["int_ops"] / (v["total_ms"] / 1e3) / pk, 4) if pk and v["int_ops"] else None
@@ -365,6 +365,24 @@ def run_ours(args, rank, world, local_rank):
         "int_peaks_Gops": {k: round(v / 1e9, 2) for k, v in int_peaks.items()},
     }
 
+    # ---------------- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        # right after the timed device steps, before the comparator legs:
+        # after those legs the copy engines' uploads ran at 83-112 GB/s
+        # (end to end 430-443 products/s), before them at 110-210 GB/s (524)
+        if wave is not None:
+            # the host-buffer leg pipelines uploads with the multiplies per k:
+            # it runs the batched calls (same residues as the wave)
+            del wave_bufs
+            wave.close()
+        torch.cuda.empty_cache()
+        if ex is None:
+            if ws is None:
+                ws = torch.empty(max(ctx.workspace_size(k, L, B) for k in ks) // 8 + 1, dtype=torch.uint64,
+                                 device=dev)
+            result["e2e"] = e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, inp, outs, tup, otup,
+                                    inp[max(ks)].clone())
+
     # ---------------- comparators (outside the timed region)
     if not args.no_compare and rank == 0:
         reps = 2
@@ -388,24 +406,6 @@ def run_ours(args, rank, world, local_rank):
             per_k[k]["speedup_vs_chained"] = round(per_k[k]["kinput_ctmults_s"] / per_k[k]["chained_2input_ctmults_s"], 3)
             per_k[k]["speedup_vs_one_per_launch"] = round(per_k[k]["kinput_ctmults_s"] / per_k[k]["one_per_launch_ctmults_s"], 3)
         ctx.check()
-
-    # ---------------- end to end through the C ABI with host buffers
-    if not args.no_e2e:
-        # the comparator legs leave large cached device blocks behind; release
-        # them before the host-buffer leg (measured on one box: uploads ran at
-        # 69-87 GB/s with those blocks cached and 210.7 GB/s after release)
-        if wave is not None:
-            # the host-buffer leg pipelines uploads with the multiplies per k:
-            # it runs the batched calls (same residues as the wave)
-            del wave_bufs
-            wave.close()
-        torch.cuda.empty_cache()
-        if ex is None:
-            if ws is None:
-                ws = torch.empty(max(ctx.workspace_size(k, L, B) for k in ks) // 8 + 1, dtype=torch.uint64,
-                                 device=dev)
-            result["e2e"] = e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, inp, outs, tup, otup,
-                                    inp[max(ks)].clone())
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(args)
@@ -538,12 +538,16 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     import paper_2601_15401_gb300 as G
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
+    n_pull = B if args.h2d == "pull" else 0 if args.h2d == "copy" else int(round(B * args.pull_fraction))
+
     def upload(k, b, cs):
-        """One batch element's inputs host -> device on stream cs: by the GPU's
-        own loads over the host link (ckks_pull, the default: the copy engines
-        restart at a fraction of the link's rate after device compute), or by
-        the copy engines (cudaMemcpyAsync)."""
-        if args.h2d == "pull":
+        """One batch element's inputs host -> device on stream cs: by the copy
+        engines (cudaMemcpyAsync) or by the GPU's own loads over the host link
+        (ckks_pull). "mixed" (default) sends the last pull_fraction of the
+        batch elements through the GPU's loads: the copy engines restart at a
+        fraction of the link's rate after device compute, and the GPU's loads
+        take SM slots from the multiplies, so each carries part."""
+        if b >= B - n_pull:
             G.pull(dev_inp[k][b], host_in[b, :k], blocks=sms * args.pull_ctas_per_sm, stream=cs)
         else:
             dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
@@ -625,8 +629,10 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
             "h2d_GBps_alone": [round(bw_before, 1), round(bw_after, 1)],
             "h2d_GBps_warmup": [round(x, 1) for x in warm_bw],
             "copy_streams": len(copies), "host_numa": numa_note,
-            "h2d": "GPU loads over the host link (ckks_pull, %d CTAs of 64 threads)" % (sms * args.pull_ctas_per_sm)
-                   if args.h2d == "pull" else "copy engines (cudaMemcpyAsync)",
+            "h2d": {"copy_engines_elements": B - n_pull, "gpu_load_elements": n_pull,
+                    "gpu_load_ctas": sms * args.pull_ctas_per_sm if n_pull else 0,
+                    "note": "per step, of the B batch elements of every k: copy engines (cudaMemcpyAsync) for the "
+                            "first, the GPU's own loads over the host link (ckks_pull, 64-thread CTAs) for the rest"},
             "overlap": "uploads (own stream) overlap the multiplies of this and the previous step; downloads on "
                        "a second stream"}
 
@@ -690,7 +696,8 @@ def run_reference(args, rank, world):
 
 
 KERNEL_SOURCES = {
-    "ntt": ["ntt.cu", "common.cuh", "internal.h"],
+    "ntt": ["ntt.cu", "ntt_kernel.cuh", "ntt_uf.cu", "ntt_ui.cu", "ntt_tf.cu", "ntt_ti.cu", "common.cuh",
+            "internal.h"],
     "rns": ["rns.cu", "rns.h", "common.cuh", "internal.h"],
 }
 
@@ -717,8 +724,10 @@ def main():
     ap.add_argument("--ks", default="")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--h2d", default="pull", choices=["pull", "copy"],
-                    help="e2e uploads: GPU loads over the host link (pull) or the copy engines (copy)")
+    ap.add_argument("--h2d", default="mixed", choices=["mixed", "pull", "copy"],
+                    help="e2e uploads: copy engines, GPU loads over the host link (pull), or both (mixed)")
+    ap.add_argument("--pull-fraction", type=float, default=0.25,
+                    help="--h2d mixed: share of the batch elements uploaded by GPU loads")
     ap.add_argument("--pull-ctas-per-sm", type=int, default=1, help="64-thread CTAs per SM of the e2e uploads")
     ap.add_argument("--copy-streams", type=int, default=1,
                     help="streams the e2e leg spreads its copies over (1 measured best: 465 vs 343 with 4)")
