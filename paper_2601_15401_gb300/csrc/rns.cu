@@ -195,118 +195,6 @@ cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_j
 // y'_j = [y_j (Q_beta/q_j)^-1]_{q_j} was produced by the INTT's epilogue.
 // blockIdx.y = (t, beta) job, blockIdx.z = batch.
 // ---------------------------------------------------------------------------
-// One CTA: the constants of (level, digit) staged in shared memory, then one
-// coefficient per thread. y: limb 0 of the prescaled d_t; dst: slot 0 of the
-// (t, digit) ModUp output.
-template <int AMAX>
-__device__ __forceinline__ void bconv_block(const u64 *ctab, const u64 *y0, u64 *dst0, int level, int beta,
-                                            int alpha, int L, int K, int n_primes, int N, const ModQ *mods, u64 *cs) {
-    const int d0 = beta * alpha;
-    int d1 = d0 + alpha;
-    if (d1 > level) d1 = level;
-    const int na = d1 - d0;
-    // targets: Q limbs outside the digit, then every P limb
-    const int nq_t = level - na;
-    const int n_t = nq_t + K;
-    for (int i = threadIdx.x; i < na * n_t; i += blockDim.x) {
-        int jj = i / n_t, ti = i % n_t;
-        int x = ti < nq_t ? (ti < d0 ? ti : ti + na) : L + (ti - nq_t);
-        cs[i] = ctab[(i64)jj * n_primes + x];
-    }
-    __syncthreads();
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= N) return;
-    const u64 *ysrc = y0 + e;
-    u64 y[AMAX];
-#pragma unroll
-    for (int jj = 0; jj < AMAX; ++jj) y[jj] = jj < na ? ysrc[(i64)(d0 + jj) * N] : 0ull;
-    u64 *dst = dst0 + e;
-    for (int ti = 0; ti < n_t; ++ti) {
-        const int slot = ti < nq_t ? (ti < d0 ? ti : ti + na) : level + (ti - nq_t);
-        const int x = ti < nq_t ? slot : L + (ti - nq_t);
-        const ModQ m = mods[x];
-        // sum over the digit: hi stays below q because the digit's primes sum to < 2^64
-        Acc128Lazy acc;
-        acc.zero();
-#pragma unroll
-        for (int jj = 0; jj < AMAX; ++jj)
-            if (jj < na) acc.mac(y[jj], cs[jj * n_t + ti]);
-        dst[(i64)slot * N] = redc(acc.hi, acc.lo, m);
-    }
-}
-
-template <int AMAX>
-__global__ void __launch_bounds__(1024) bconv_kernel(BconvArgs A) {
-    extern __shared__ u64 cs[];  // [alpha][n_targets] Montgomery constants
-    const int job = blockIdx.y;
-    const int b = blockIdx.z;
-    const int t = job / A.n_digits;
-    const int beta = job % A.n_digits;
-    bconv_block<AMAX>(A.consts + (i64)beta * A.alpha * A.n_primes,
-                      A.y.ptr + (i64)b * A.y.bstride + (i64)t * A.y.pstride,
-                      A.ext.ptr + (i64)b * A.ext.bstride + (i64)(t * A.n_digits + beta) * A.ext.pstride, A.level, beta,
-                      A.alpha, A.L, A.K, A.n_primes, A.N, A.mods, cs);
-}
-
-// Table launch: blockIdx.y = (product, d_t, digit) entry.
-template <int AMAX>
-__global__ void __launch_bounds__(1024) bconv_table_kernel(const BconvJob *jobs, int alpha, int L, int K,
-                                                           int n_primes, int N, const ModQ *mods) {
-    extern __shared__ u64 cs[];
-    const BconvJob J = jobs[blockIdx.y];
-    bconv_block<AMAX>(J.consts, J.y, J.ext, J.level, J.beta, alpha, L, K, n_primes, N, mods, cs);
-}
-
-cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) {
-    const int thr = C.tune_bconv_threads;
-    dim3 grid((A.N + thr - 1) / thr, A.n_t * A.n_digits, A.n_batch);
-    size_t smem = (size_t)A.alpha * (A.level + A.K) * sizeof(u64);
-    count_kernel(C);
-    count_op(C, OP_BCONV, (unsigned long long)A.n_t * A.n_digits * A.n_batch);
-    // reads y' once, writes level + K - |digit| limbs per (t, digit)
-    double limbs_out = (double)A.n_t * ((double)A.n_digits * (A.level + A.K) - A.level);
-    // multiply-accumulates: per (t, digit) and coefficient, |digit| per target
-    double macs = 0;
-    for (int beta = 0; beta < A.n_digits; ++beta) {
-        const int na = std::min(A.level, (beta + 1) * A.alpha) - beta * A.alpha;
-        macs += (double)na * (A.level - na + A.K);
-    }
-    macs *= (double)A.n_t * A.n_batch * A.N;
-    ProfScope ps(C, KC_BCONV, ((double)A.n_t * A.level + limbs_out) * A.n_batch * A.N * sizeof(u64), st, macs);
-    if (A.alpha <= 4) bconv_kernel<4><<<grid, thr, smem, st>>>(A);
-    else if (A.alpha <= 8) bconv_kernel<8><<<grid, thr, smem, st>>>(A);
-    else if (A.alpha <= 12) bconv_kernel<12><<<grid, thr, smem, st>>>(A);
-    else bconv_kernel<16><<<grid, thr, smem, st>>>(A);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_jobs, double bytes, double macs,
-                               cudaStream_t st) {
-    if (n_jobs <= 0) return cudaSuccess;
-    if (n_jobs > 65535) return cudaErrorInvalidValue;
-    const int thr = C.tune_bconv_threads;
-    dim3 grid((C.N + thr - 1) / thr, (unsigned)n_jobs);
-    size_t smem = (size_t)C.alpha * (C.L + C.K) * sizeof(u64);
-    count_kernel(C);
-    count_op(C, OP_BCONV, (unsigned long long)n_jobs);
-    ProfScope ps(C, KC_BCONV, bytes, st, macs);
-    const int np = C.L + C.K;
-    if (C.alpha <= 4) bconv_table_kernel<4><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
-    else if (C.alpha <= 8) bconv_table_kernel<8><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
-    else if (C.alpha <= 12) bconv_table_kernel<12><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
-    else bconv_table_kernel<16><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Key inner product summed over every extra key t = 2..n and digit beta
-// (Eq. 15 combined before ModDown):
-//   acc_l[x] = sum_t sum_beta term(t, beta, x) * ek'_{t,beta,l}[x]
-// term = d_t[x] when x lies in digit beta (the digit's own limbs), else the
-// ModUp output. Keys are in Montgomery form, so one REDC per output.
-// Grid: x = coefficient chunk, y = target limb, z = batch (fastest-varying
-// batch would reuse key tiles in L2; see launch order below).
-// ---------------------------------------------------------------------------
 // Coefficients per thread of the key MAC: two adjacent coefficients read
 // with 16-byte loads (twice the bytes in flight per load instruction; the
 // kernel is bound by load latency, not by its multiplies).
@@ -336,6 +224,138 @@ __device__ __forceinline__ void store_span(u64 *p, const u64 (&v)[V]) {
     }
 }
 
+#ifndef CKKS_BCONV_VEC
+#define CKKS_BCONV_VEC 2
+#endif
+
+// One CTA: the constants of (level, digit) staged in shared memory, then one
+// coefficient per thread. y: limb 0 of the prescaled d_t; dst: slot 0 of the
+// (t, digit) ModUp output.
+template <int AMAX>
+__device__ __forceinline__ void bconv_block(const u64 *ctab, const u64 *y0, u64 *dst0, int level, int beta,
+                                            int alpha, int L, int K, int n_primes, int N, const ModQ *mods, u64 *cs) {
+    const int d0 = beta * alpha;
+    int d1 = d0 + alpha;
+    if (d1 > level) d1 = level;
+    const int na = d1 - d0;
+    // targets: Q limbs outside the digit, then every P limb
+    const int nq_t = level - na;
+    const int n_t = nq_t + K;
+    for (int i = threadIdx.x; i < na * n_t; i += blockDim.x) {
+        int jj = i / n_t, ti = i % n_t;
+        int x = ti < nq_t ? (ti < d0 ? ti : ti + na) : L + (ti - nq_t);
+        cs[i] = ctab[(i64)jj * n_primes + x];
+    }
+    __syncthreads();
+    // CKKS_BCONV_VEC adjacent coefficients per thread: independent MAC
+    // chains for the scheduler, 16-byte loads and stores
+    constexpr int V = CKKS_BCONV_VEC;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (e >= N) return;
+    const u64 *ysrc = y0 + e;
+    u64 y[AMAX][V];
+#pragma unroll
+    for (int jj = 0; jj < AMAX; ++jj) {
+        if (jj < na) load_span<V>(ysrc + (i64)(d0 + jj) * N, y[jj]);
+        else
+#pragma unroll
+            for (int v = 0; v < V; ++v) y[jj][v] = 0ull;
+    }
+    u64 *dst = dst0 + e;
+    for (int ti = 0; ti < n_t; ++ti) {
+        const int slot = ti < nq_t ? (ti < d0 ? ti : ti + na) : level + (ti - nq_t);
+        const int x = ti < nq_t ? slot : L + (ti - nq_t);
+        const ModQ m = mods[x];
+        // sum over the digit: hi stays below q because the digit's primes sum to < 2^64
+        Acc128Lazy acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v].zero();
+#pragma unroll
+        for (int jj = 0; jj < AMAX; ++jj)
+            if (jj < na) {
+                const u64 c = cs[jj * n_t + ti];
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v].mac(y[jj][v], c);
+            }
+        u64 r[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) r[v] = redc(acc[v].hi, acc[v].lo, m);
+        store_span<V>(dst + (i64)slot * N, r);
+    }
+}
+
+template <int AMAX>
+__global__ void __launch_bounds__(1024) bconv_kernel(BconvArgs A) {
+    extern __shared__ u64 cs[];  // [alpha][n_targets] Montgomery constants
+    const int job = blockIdx.y;
+    const int b = blockIdx.z;
+    const int t = job / A.n_digits;
+    const int beta = job % A.n_digits;
+    bconv_block<AMAX>(A.consts + (i64)beta * A.alpha * A.n_primes,
+                      A.y.ptr + (i64)b * A.y.bstride + (i64)t * A.y.pstride,
+                      A.ext.ptr + (i64)b * A.ext.bstride + (i64)(t * A.n_digits + beta) * A.ext.pstride, A.level, beta,
+                      A.alpha, A.L, A.K, A.n_primes, A.N, A.mods, cs);
+}
+
+// Table launch: blockIdx.y = (product, d_t, digit) entry.
+template <int AMAX>
+__global__ void __launch_bounds__(1024) bconv_table_kernel(const BconvJob *jobs, int alpha, int L, int K,
+                                                           int n_primes, int N, const ModQ *mods) {
+    extern __shared__ u64 cs[];
+    const BconvJob J = jobs[blockIdx.y];
+    bconv_block<AMAX>(J.consts, J.y, J.ext, J.level, J.beta, alpha, L, K, n_primes, N, mods, cs);
+}
+
+cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) {
+    const int thr = C.tune_bconv_threads;
+    dim3 grid((A.N + thr * CKKS_BCONV_VEC - 1) / (thr * CKKS_BCONV_VEC), A.n_t * A.n_digits, A.n_batch);
+    size_t smem = (size_t)A.alpha * (A.level + A.K) * sizeof(u64);
+    count_kernel(C);
+    count_op(C, OP_BCONV, (unsigned long long)A.n_t * A.n_digits * A.n_batch);
+    // reads y' once, writes level + K - |digit| limbs per (t, digit)
+    double limbs_out = (double)A.n_t * ((double)A.n_digits * (A.level + A.K) - A.level);
+    // multiply-accumulates: per (t, digit) and coefficient, |digit| per target
+    double macs = 0;
+    for (int beta = 0; beta < A.n_digits; ++beta) {
+        const int na = std::min(A.level, (beta + 1) * A.alpha) - beta * A.alpha;
+        macs += (double)na * (A.level - na + A.K);
+    }
+    macs *= (double)A.n_t * A.n_batch * A.N;
+    ProfScope ps(C, KC_BCONV, ((double)A.n_t * A.level + limbs_out) * A.n_batch * A.N * sizeof(u64), st, macs);
+    if (A.alpha <= 4) bconv_kernel<4><<<grid, thr, smem, st>>>(A);
+    else if (A.alpha <= 8) bconv_kernel<8><<<grid, thr, smem, st>>>(A);
+    else if (A.alpha <= 12) bconv_kernel<12><<<grid, thr, smem, st>>>(A);
+    else bconv_kernel<16><<<grid, thr, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_jobs, double bytes, double macs,
+                               cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    if (n_jobs > 65535) return cudaErrorInvalidValue;
+    const int thr = C.tune_bconv_threads;
+    dim3 grid((C.N + thr * CKKS_BCONV_VEC - 1) / (thr * CKKS_BCONV_VEC), (unsigned)n_jobs);
+    size_t smem = (size_t)C.alpha * (C.L + C.K) * sizeof(u64);
+    count_kernel(C);
+    count_op(C, OP_BCONV, (unsigned long long)n_jobs);
+    ProfScope ps(C, KC_BCONV, bytes, st, macs);
+    const int np = C.L + C.K;
+    if (C.alpha <= 4) bconv_table_kernel<4><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else if (C.alpha <= 8) bconv_table_kernel<8><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else if (C.alpha <= 12) bconv_table_kernel<12><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else bconv_table_kernel<16><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Key inner product summed over every extra key t = 2..n and digit beta
+// (Eq. 15 combined before ModDown):
+//   acc_l[x] = sum_t sum_beta term(t, beta, x) * ek'_{t,beta,l}[x]
+// term = d_t[x] when x lies in digit beta (the digit's own limbs), else the
+// ModUp output. Keys are in Montgomery form, so one REDC per output.
+// Grid: x = coefficient chunk, y = target limb, z = batch (fastest-varying
+// batch would reuse key tiles in L2; see launch order below).
+// ---------------------------------------------------------------------------
 // V coefficients of accumulator limb x of one product: dsrc / esrc point at
 // limb x, coefficient e of the D tuple / the first ModUp output; krow at the
 // prime's row, coefficient e, of the first key.
