@@ -416,7 +416,7 @@ def op_unit(kernel_class: str) -> str:
     """The integer operation a kernel class is built from (its roofline unit)."""
     if kernel_class.startswith("ntt"):
         return "butterfly"
-    if kernel_class in ("bconv", "key_mac"):
+    if kernel_class in ("bconv", "key_mac", "tensor"):
         return "mac128"
     return ""
 

@@ -414,8 +414,9 @@ int ckks_counters(ckks_context *ctx, ckks_op_counters *out, int reset);
  * integer work: for the NTT / INTT phases the 64-bit Shoup products (one per
  * butterfly, log2(n)/2 per element of an n-point phase, plus one per element
  * for each fused scaling), for BConv and the key MAC the 64 x 64 -> 128-bit
- * multiply-accumulates (Eq. 4 and Eq. 15 summed term by term); 0 for the
- * other classes. */
+ * multiply-accumulates (Eq. 4 and Eq. 15 summed term by term), for the
+ * tensor product (Eq. 13) its 64 x 64 products and modular reductions; 0
+ * for the other classes. */
 typedef struct {
     char name[24];
     uint64_t launches;

@@ -151,6 +151,22 @@ __global__ void __launch_bounds__(kThreads) tensor_table_kernel(const TensorJob 
     tensor_coeff<MAXT>(TensorTableView{J}, r, j, mods[j], rpow);
 }
 
+// 64 x 64 -> 128-bit products per coefficient of a node's tensor product
+// (Karatsuba pairs when a ciphertext multiplies the running tuple: 3 per
+// pair, 2 for an unpaired term; schoolbook otherwise), plus one reduction
+// per term of every intermediate and of the output (counted alike).
+double tensor_products_per_coeff(const int *polys, int m) {
+    double ops = 0;
+    int ncur = polys[0];
+    for (int c = 1; c < m; ++c) {
+        const int ny = polys[c];
+        ops += ny == 2 ? 3.0 * (ncur / 2) + 2.0 * (ncur % 2) : (double)ncur * ny;
+        ncur += ny - 1;
+        ops += ncur;  // REDC of every term
+    }
+    return ops + ncur;  // the final R^m correction
+}
+
 cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t st) {
     TensorArgs A = Ain;
     A.log_n = C.log_n;
@@ -163,7 +179,9 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t 
     }
     int out_polys = in_polys - A.m + 1;
     maxt = std::max(maxt, out_polys);
-    ProfScope ps(C, KC_TENSOR, (double)(in_polys + out_polys) * A.n_batch * A.level * A.N * sizeof(u64), st);
+    const double coeffs = (double)A.n_batch * A.level * A.N;
+    ProfScope ps(C, KC_TENSOR, (double)(in_polys + out_polys) * coeffs * sizeof(u64), st,
+                 coeffs * tensor_products_per_coeff(A.child_polys, A.m));
     if (maxt <= 3) tensor_kernel<3><<<blocks, kThreads, 0, st>>>(A);
     else if (maxt <= 4) tensor_kernel<4><<<blocks, kThreads, 0, st>>>(A);
     else if (maxt <= 5) tensor_kernel<5><<<blocks, kThreads, 0, st>>>(A);
@@ -174,12 +192,12 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t 
 }
 
 cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_jobs, int maxt, int max_level,
-                                double bytes, cudaStream_t st) {
+                                double bytes, double ops, cudaStream_t st) {
     if (n_jobs <= 0) return cudaSuccess;
     if (n_jobs > 65535) return cudaErrorInvalidValue;
     dim3 blocks((unsigned)(((i64)max_level * C.N + kThreads - 1) / kThreads), (unsigned)n_jobs);
     count_kernel(C);
-    ProfScope ps(C, KC_TENSOR, bytes, st);
+    ProfScope ps(C, KC_TENSOR, bytes, st, ops);
     if (maxt <= 3) tensor_table_kernel<3><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
     else if (maxt <= 4) tensor_table_kernel<4><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
     else if (maxt <= 5) tensor_table_kernel<5><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);

@@ -90,7 +90,8 @@ struct MacTarget {                       // one accumulator limb x of product `j
 
 cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st);
 cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_jobs, int maxt, int max_level,
-                                double bytes, cudaStream_t st);
+                                double bytes, double ops, cudaStream_t st);
+double tensor_products_per_coeff(const int *polys, int m);
 cudaError_t launch_rschain_table(const Context &C, const RsJob *jobs, int n_jobs, int max_polys, double bytes,
                                  cudaStream_t st);
 cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_jobs, double bytes, double macs,

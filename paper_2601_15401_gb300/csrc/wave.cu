@@ -220,6 +220,7 @@ void build_product(Builder &B, const WaveProduct &w, Bump &ws) {
             s.maxt = std::max(s.maxt, maxt);
             s.max_level = std::max(s.max_level, lv);
             s.bytes += (double)(in_polys + np) * lv * limb;
+            s.ops += (double)lv * N * tensor_products_per_coeff(T.cpolys, T.m);
         }
         if (!nd.root) {
             // Algorithm 1 in place on D (np polynomials, level lv, mu = nd.mu)
@@ -473,7 +474,7 @@ cudaError_t enqueue(ckks_wave &W, char *ws /* the job tables */, cudaStream_t st
                                        st);
             break;
         case SK_TENSOR:
-            e = launch_tensor_table(C, (const TensorJob *)(ws + s.off), n, s.maxt, s.max_level, s.bytes, st);
+            e = launch_tensor_table(C, (const TensorJob *)(ws + s.off), n, s.maxt, s.max_level, s.bytes, s.ops, st);
             break;
         case SK_RSCHAIN:
             e = launch_rschain_table(C, (const RsJob *)(ws + s.off), n, s.max_polys, s.bytes, st);
