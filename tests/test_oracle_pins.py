@@ -409,14 +409,29 @@ def test_encode_decode_roundtrip_and_slot_product():
 # --------------------------------------------------------------------------
 # partitions (Section V-C, Table II)
 # --------------------------------------------------------------------------
-TABLE_II_RS = {3: (3, 0), 4: (6, 6), 5: (11, 6), 6: (14, 8), 7: (18, 15), 8: (22, 22),
-               9: (31, 12), 10: (34, 19), 11: (38, 26), 12: (42, 30)}
+def _golden_table_ii():
+    """Rows of tests/golden/table2_partitions.txt: k -> (baseline RS units,
+    proposed RS units, proposed partition or None)."""
+    import os
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_partitions.txt")
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        k, base, prop, part = int(line[0]), int(line[1]), int(line[2]), line[3]
+        rows[k] = (base, prop, None if part == "-" else part)
+    return rows
 
 
-@pytest.mark.parametrize("k", sorted(TABLE_II_RS))
+TABLE_II_ROWS = _golden_table_ii()
+
+
+@pytest.mark.parametrize("k", sorted(k for k in TABLE_II_ROWS if k <= 12))
 def test_table_ii_rescale_units(k):
-    base, prop = TABLE_II_RS[k]
-    root = plan.parse(plan.TABLE_II[k], k)
+    base, prop, part = TABLE_II_ROWS[k]
+    assert plan.TABLE_II[k] == part
+    root = plan.parse(part, k)
     assert plan.valid(root, k)
     assert plan.rs_units(root) == prop
     assert plan.rs_units(plan.binary_partition(k)) == base
@@ -424,10 +439,11 @@ def test_table_ii_rescale_units(k):
 
 
 def test_17_input_example():
+    base, prop, _ = TABLE_II_ROWS[17]
     b = plan.binary_partition(17)
-    assert plan.rs_units(b) == 79
+    assert plan.rs_units(b) == base == 79
     assert plan.rs_units(b.children[0]) - 17 == 62 or plan.rs_units(plan.binary_partition(16)) == 62
-    assert plan.min_rs_units(17) == 41
+    assert plan.min_rs_units(17) == prop == 41
 
 
 def test_6_input_depth_rule():
