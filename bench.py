@@ -371,13 +371,12 @@ def run_ours(args, rank, world, local_rank):
         # after those legs the copy engines' uploads ran at 83-112 GB/s
         # (end to end 430-443 products/s), before them at 110-210 GB/s (524)
         if wave is not None:
-            # the host-buffer leg pipelines uploads with the multiplies per k:
-            # it runs the batched calls (same residues as the wave)
+            # the host-buffer leg builds its own two waves over two buffer sets
             del wave_bufs
             wave.close()
         torch.cuda.empty_cache()
         if ex is None:
-            if ws is None:
+            if ws is None and args.engine != "waves":
                 ws = torch.empty(max(ctx.workspace_size(k, L, B) for k in ks) // 8 + 1, dtype=torch.uint64,
                                  device=dev)
             result["e2e"] = e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, inp, outs, tup, otup,
@@ -508,9 +507,13 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     """The step through the C ABI with host buffers: every k's inputs are
     copied from pinned host memory, multiplied, and the outputs copied back,
     all inside the timed region. Uploads run on their own stream(s) and
-    overlap the multiplies (each k has its own device buffers, so an upload
-    waits only for the previous multiply that read them); downloads run on a
-    second stream after their multiply."""
+    overlap the multiplies; downloads run on a second stream.
+
+    With --engine batch each k has its own device buffers, so an upload
+    waits only for the previous multiply of that k. With --engine waves the
+    step is one cross-shape wave, and two sets of device buffers alternate
+    between steps: step i's uploads fill one set while step i-1's wave reads
+    the other."""
     import torch
     kmax = max(ks)
     # pinned host buffers on the GPU's own NUMA node: allocate them from a
@@ -539,6 +542,30 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     n_pull = B if args.h2d == "pull" else 0 if args.h2d == "copy" else int(round(B * args.pull_fraction))
+    # device buffer sets (inputs, outputs): one for the batched engine, two
+    # alternating sets for the wave engine
+    sets = [(dev_inp, dev_out)]
+    waves_mode = args.engine == "waves"
+    cur_set = [0]
+    if waves_mode:
+        inp1 = {k: torch.empty_like(dev_inp[k]) for k in ks}
+        out1 = {k: torch.empty_like(dev_out[k]) for k in ks}
+        sets.append((inp1, out1))
+        waves, wave_tables = [], []
+        for si, (inps, outs_) in enumerate(sets):
+            items = [([G.Tuple(inps[k][b, u], 2, L, L, 1, 2.0 ** 50) for u in range(k)],
+                      G.Tuple(outs_[k][b], 2, L - depth[k], L - depth[k]), None) for k in ks for b in range(B)]
+            w = G.Wave(ctx, items, evk)
+            waves.append(w)
+            wave_tables.append(torch.empty(w.workspace_size()[0] // 8 + 32, dtype=torch.uint64, device=dev))
+        wave_scratch = torch.empty(max(w.workspace_size()[1] for w in waves) // 8 + 32, dtype=torch.uint64,
+                                   device=dev)
+        for w, t in zip(waves, wave_tables):
+            w.run(t, wave_scratch, stream=stream)  # writes each wave's job tables
+        torch.cuda.synchronize()
+        set_used = [None, None]  # set -> event: the last wave that read its inputs
+        set_down = [None, None]  # set -> event: the last download of its outputs
+        step_no = [0]
 
     def upload(k, b, cs):
         """One batch element's inputs host -> device on stream cs: by the copy
@@ -547,12 +574,49 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
         batch elements through the GPU's loads: the copy engines restart at a
         fraction of the link's rate after device compute, and the GPU's loads
         take SM slots from the multiplies, so each carries part."""
+        dst = sets[cur_set[0]][0][k][b]
         if b >= B - n_pull:
-            G.pull(dev_inp[k][b], host_in[b, :k], blocks=sms * args.pull_ctas_per_sm, stream=cs)
+            G.pull(dst, host_in[b, :k], blocks=sms * args.pull_ctas_per_sm, stream=cs)
         else:
-            dev_inp[k][b].copy_(host_in[b, :k], non_blocking=True)
+            dst.copy_(host_in[b, :k], non_blocking=True)
+
+    def step_waves():
+        p = step_no[0] & 1
+        step_no[0] += 1
+        cur_set[0] = p
+        evs = []
+        for c, cs in enumerate(copies):
+            if set_used[p] is not None:
+                cs.wait_event(set_used[p])
+            with torch.cuda.stream(cs):
+                for k in ks:
+                    for b in range(c, B, len(copies)):
+                        upload(k, b, cs)
+                e = torch.cuda.Event()
+                e.record(cs)
+                evs.append(e)
+        for e in evs:
+            stream.wait_event(e)
+        if set_down[p] is not None:
+            stream.wait_event(set_down[p])  # this set's outputs from two steps back are on the host
+        waves[p].run(wave_tables[p], wave_scratch, stream=stream)
+        done = torch.cuda.Event()
+        done.record(stream)
+        set_used[p] = done
+        down.wait_event(done)
+        with torch.cuda.stream(down):
+            for k in ks:
+                host_out[k].copy_(sets[p][1][k], non_blocking=True)
+        fin = torch.cuda.Event()
+        fin.record(down)
+        set_down[p] = fin
+        last_fin[0] = fin
+
+    last_fin = [None]
 
     def step():
+        if waves_mode:
+            return step_waves()
         up = {}
         for k in ks:
             evs = []
@@ -611,16 +675,20 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize()
+    cur_set[0] = 0
     bw_before = upload_alone()
     steps = max(1, args.steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
         step()
+    if last_fin[0] is not None:
+        stream.wait_event(last_fin[0])  # the last step's downloads are inside the timed region
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
     ms = reduce_max(ms, world, dev)
+    cur_set[0] = 0
     bw_after = upload_alone()
     os.sched_setaffinity(0, prev_affinity)
     ctx.check()
@@ -633,6 +701,8 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
                     "gpu_load_ctas": sms * args.pull_ctas_per_sm if n_pull else 0,
                     "note": "per step, of the B batch elements of every k: copy engines (cudaMemcpyAsync) for the "
                             "first, the GPU's own loads over the host link (ckks_pull, 64-thread CTAs) for the rest"},
+            "engine": "one cross-shape wave per step, two alternating input / output sets" if waves_mode else
+                      "one batched call per k",
             "overlap": "uploads (own stream) overlap the multiplies of this and the previous step; downloads on "
                        "a second stream"}
 

@@ -461,6 +461,9 @@ struct PhaseLaunch {
 #ifndef CKKS_NTT_FAST_MINB
 #define CKKS_NTT_FAST_MINB 3    // fixed modes: 80 registers, three CTAs per SM
 #endif
+#ifndef CKKS_NTT_EQ17_MINB
+#define CKKS_NTT_EQ17_MINB 2    // the Eq. 17 load spills at 80 registers: two CTAs per SM
+#endif
 
 template <typename K>
 static inline cudaError_t allow_smem(K kern, size_t smem) {
@@ -511,7 +514,7 @@ static inline cudaError_t dispatch_phase(bool cols, int logn, const NttPhase &P,
         if constexpr (FWD) {                                                                       \
             if (cols && S.mode == ST_LAZY) {                                                       \
                 if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB); \
-                if (L.mode == LD_EQ17) CKKS_LAUNCH(LG, true, LD_EQ17, ST_LAZY, CKKS_NTT_MINB);        \
+                if (L.mode == LD_EQ17) CKKS_LAUNCH(LG, true, LD_EQ17, ST_LAZY, CKKS_NTT_EQ17_MINB);   \
             }                                                                                      \
             if (!cols && L.mode == LD_PLAIN) {                                                     \
                 if (S.mode == ST_REDUCE) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_REDUCE, CKKS_NTT_FAST_MINB); \
