@@ -376,7 +376,7 @@ def run_ours(args, rank, world, local_rank):
             wave.close()
         torch.cuda.empty_cache()
         if ex is None:
-            if ws is None and args.engine != "waves":
+            if ws is None and args.e2e_engine != "waves":
                 ws = torch.empty(max(ctx.workspace_size(k, L, B) for k in ks) // 8 + 1, dtype=torch.uint64,
                                  device=dev)
             result["e2e"] = e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, inp, outs, tup, otup,
@@ -545,7 +545,7 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     # device buffer sets (inputs, outputs): one for the batched engine, two
     # alternating sets for the wave engine
     sets = [(dev_inp, dev_out)]
-    waves_mode = args.engine == "waves"
+    waves_mode = args.e2e_engine == "waves"
     cur_set = [0]
     if waves_mode:
         inp1 = {k: torch.empty_like(dev_inp[k]) for k in ks}
@@ -805,7 +805,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--tune", action="append", default=[], help="key=value library tunable (skips the autotuner)")
     ap.add_argument("--streams", type=int, default=1)
-    ap.add_argument("--engine", default="batch", choices=["batch", "waves"],
+    ap.add_argument("--e2e-engine", default="batch", choices=["batch", "waves"],
+                    help="engine of the host-buffer leg: one batched call per k (uploads of each k overlap the "
+                         "multiplies of the others) or one wave per step over two alternating buffer sets")
+    ap.add_argument("--engine", default="waves", choices=["batch", "waves"],
                     help="batch: one batched call per k; waves: the whole step as one cross-shape wave")
     args = ap.parse_args()
     world = env_int("WORLD_SIZE", 1)

@@ -583,14 +583,16 @@ def pull(dst, src, nbytes: int | None = None, blocks: int = 0, stream=None):
                            _stream(stream)), "ckks_pull")
 
 
-PEAK_KINDS = {"shoup": 0, "butterfly": 1, "mac128": 2, "montgomery": 3, "transpose_shfl": 4, "transpose_smem": 5}
+PEAK_KINDS = {"shoup": 0, "butterfly": 1, "mac128": 2, "montgomery": 3, "transpose_shfl": 4, "transpose_smem": 5,
+              "butterfly_q1": 6, "shoup_q1": 7}
 
 
 def peak_int(kind: str, q: int, blocks: int, threads: int = 256, iters: int = 4096, reps: int = 5,
              stream=None) -> float:
     """Measured rate (operations per second, best of `reps` CUDA-event timed
     launches after one warm-up) of one integer operation of the hot path on
-    this GPU: "shoup", "butterfly", "mac128" or "montgomery" (ckks_peak_int)."""
+    this GPU: "shoup", "butterfly", "mac128" or "montgomery" (ckks_peak_int);
+    "shoup_q1" / "butterfly_q1" for a modulus q = 1 (mod 2^32)."""
     import torch
     chains = lib().ckks_peak_chains()
     w = [(q - 1 - 977 * i) % q for i in range(chains)]
@@ -610,7 +612,7 @@ def peak_int(kind: str, q: int, blocks: int, threads: int = 256, iters: int = 40
         ms = e0.elapsed_time(e1)
         if r and (best is None or ms < best):
             best = ms
-    per_thread = 16 if PEAK_KINDS[kind] >= 4 else chains
+    per_thread = 16 if PEAK_KINDS[kind] in (4, 5) else chains
     return blocks * threads * per_thread * iters / (best / 1e3)
 
 

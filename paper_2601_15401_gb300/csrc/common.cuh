@@ -32,6 +32,16 @@ __device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 wp, u64 q) {
     return x * w - mulhi64(x, wp) * q;
 }
 
+// The same for a modulus q = 1 (mod 2^32), q = qh 2^32 + 1: with
+// h = floor(x w'/2^64), h q = h + h qh 2^32, so modulo 2^64 the quotient
+// product needs only the low 32 bits of h qh (one 32-bit multiply instead of
+// a 64 x 64-bit low product).
+__device__ __forceinline__ u64 shoup_lazy_q1(u64 x, u64 w, u64 wp, uint32_t qh) {
+    const u64 h = mulhi64(x, wp);
+    const uint32_t t = (uint32_t)h * qh;
+    return x * w - h - ((u64)t << 32);
+}
+
 __device__ __forceinline__ u64 reduce2(u64 x, u64 q) { return x >= q ? x - q : x; }
 
 __device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wp, u64 q) {

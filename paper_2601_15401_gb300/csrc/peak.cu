@@ -13,6 +13,8 @@
 //           shuffles: four XOR stages of 8 swaps, no barrier
 //   kind 5  the same exchange through shared memory (store, __syncwarp,
 //           load), the way the NTT kernels pass data between passes
+//   kind 6  kind 1 for a modulus q = 1 (mod 2^32) (shoup_lazy_q1)
+//   kind 7  kind 0 for a modulus q = 1 (mod 2^32)
 // Kinds 4 and 5 count one operation per value moved.
 // Each thread runs kChains independent dependency chains so that issue, not
 // latency, limits the rate. The caller times the launch (CUDA events) and
@@ -33,6 +35,14 @@ __device__ __forceinline__ void ct_bfly_peak(u64 &X, u64 &Y, u64 w, u64 wp, u64 
     const u64 q2 = q << 1;
     const u64 x = X >= q2 ? X - q2 : X;
     const u64 t = shoup_lazy(Y, w, wp, q);
+    X = x + t;
+    Y = x - t + q2;
+}
+
+__device__ __forceinline__ void ct_bfly_peak_q1(u64 &X, u64 &Y, u64 w, u64 wp, u64 q) {
+    const u64 q2 = q << 1;
+    const u64 x = X >= q2 ? X - q2 : X;
+    const u64 t = shoup_lazy_q1(Y, w, wp, (uint32_t)(q >> 32));
     X = x + t;
     Y = x - t + q2;
 }
@@ -81,6 +91,10 @@ __global__ void __launch_bounds__(256) peak_kernel(PeakConsts P, int iters, u64 
                 x[i] = shoup_lazy(x[i], P.w[i], P.wp[i], q);
             } else if (KIND == 1) {
                 ct_bfly_peak(x[i], y[i], P.w[i], P.wp[i], q);
+            } else if (KIND == 6) {
+                ct_bfly_peak_q1(x[i], y[i], P.w[i], P.wp[i], q);
+            } else if (KIND == 7) {
+                x[i] = shoup_lazy_q1(x[i], P.w[i], P.wp[i], (uint32_t)(q >> 32));
             } else if (KIND == 2) {
                 acc[i].mac(x[i], P.w[i]);
                 x[i] += y[i];
@@ -129,9 +143,10 @@ extern "C" int ckks_peak_chains(void) { return kChains; }
 
 extern "C" int ckks_peak_int(int kind, uint64_t q, const uint64_t *w, const uint64_t *wp, int blocks, int threads,
                              int iters, uint64_t *out, void *stream) {
-    if (kind < 0 || kind > 5 || !w || !wp || !out || blocks < 1 || threads < 32 || threads > 256 ||
+    if (kind < 0 || kind > 7 || !w || !wp || !out || blocks < 1 || threads < 32 || threads > 256 ||
         threads % 32 || iters < 1 || q < 3 || q >= (1ull << 62) || !(q & 1))
         return CKKS_EINVAL;
+    if ((kind == 6 || kind == 7) && (q & 0xffffffffull) != 1) return CKKS_EINVAL;
     PeakConsts P;
     P.q = q;
     u64 inv = 1;  // q^-1 mod 2^64 by Newton's iteration (q odd)
@@ -148,6 +163,8 @@ extern "C" int ckks_peak_int(int kind, uint64_t q, const uint64_t *w, const uint
     case 1: peak_kernel<1><<<blocks, threads, 0, st>>>(P, iters, (u64 *)out); break;
     case 2: peak_kernel<2><<<blocks, threads, 0, st>>>(P, iters, (u64 *)out); break;
     case 3: peak_kernel<3><<<blocks, threads, 0, st>>>(P, iters, (u64 *)out); break;
+    case 6: peak_kernel<6><<<blocks, threads, 0, st>>>(P, iters, (u64 *)out); break;
+    case 7: peak_kernel<7><<<blocks, threads, 0, st>>>(P, iters, (u64 *)out); break;
     case 4: exchange_kernel<4><<<blocks, threads, 0, st>>>(iters, (u64 *)out); break;
     default: exchange_kernel<5><<<blocks, threads, 0, st>>>(iters, (u64 *)out); break;
     }

@@ -67,19 +67,20 @@ def is_prime(n: int) -> bool:
 NTT_CONGRUENCE = 1 << 17  # q = 1 mod 2^17 serves every N <= 2^16
 
 
-def prime_chain(bits: int, count: int, exclude=()) -> list[int]:
-    """The `count` largest primes below 2^bits with q = 1 (mod 2^17), descending."""
+def prime_chain(bits: int, count: int, exclude=(), congruence: int = NTT_CONGRUENCE) -> list[int]:
+    """The `count` largest primes below 2^bits with q = 1 (mod congruence),
+    descending (congruence a power of two >= 2N)."""
     out = []
     excl = set(exclude)
-    c = ((1 << bits) - 1) // NTT_CONGRUENCE * NTT_CONGRUENCE + 1
+    c = ((1 << bits) - 1) // congruence * congruence + 1
     if c >= (1 << bits):
-        c -= NTT_CONGRUENCE
+        c -= congruence
     while len(out) < count:
         if c < (1 << (bits - 1)):
             raise ValueError("ran out of primes")
         if c not in excl and is_prime(c):
             out.append(c)
-        c -= NTT_CONGRUENCE
+        c -= congruence
     return out
 
 
