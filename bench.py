@@ -238,7 +238,9 @@ def run_ours(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     ctx.check()
-    int_peaks = measure_int_peaks(G, params)
+    q1_forms = all(int(x) % (1 << 32) == 1 for x in list(params.q) + list(params.p)) and \
+        ctx.tune_get("q1_forms") == 1
+    int_peaks = measure_int_peaks(G, params, q1_forms)
     barrier()
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -300,7 +302,9 @@ def run_ours(args, rank, world, local_rank):
                     "traffic": traffic,
                     "peak_source": "measured in this run (ckks_peak_int: register-only stream of lazy NTT butterflies "
                                    "/ 128-bit MACs over every SM, CUDA events, best of 5), the integer-multiply "
-                                   "roofline of this GPU for the operation the kernel is built from",
+                                   "roofline of this GPU for the operation the kernel is built from"
+                                   + (", the butterfly in the Shoup form for primes = 1 mod 2^32 that the kernels run"
+                                      if q1_forms else ""),
                     "alg_ops_per_launch": st["int_ops"] / st["launches"],
                     "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
                     "avg_launch_us": st["total_ms"] * 1e3 / st["launches"],
@@ -420,15 +424,22 @@ def op_unit(kernel_class: str) -> str:
     return ""
 
 
-def measure_int_peaks(G, params) -> dict:
+def measure_int_peaks(G, params, q1: bool) -> dict:
     """Rate of the lazy NTT butterfly and of the 128-bit MAC on this GPU
     (register-only kernels over every SM; operations/s), taken at the same
-    point of the run as the timed steps."""
+    point of the run as the timed steps. The butterfly is measured in the
+    form the NTT kernels run (q1: the Shoup product for q = 1 mod 2^32);
+    with q1 the general form's rate is reported beside it."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     q = int(params.q[0])
-    return {u: max(G.peak_int(u, q, blocks=sms * per_sm, threads=256, iters=2048) for per_sm in (8, 16))
-            for u in ("butterfly", "mac128")}
+
+    def rate(u):
+        return max(G.peak_int(u, q, blocks=sms * per_sm, threads=256, iters=2048) for per_sm in (8, 16))
+    out = {"butterfly": rate("butterfly_q1" if q1 else "butterfly"), "mac128": rate("mac128")}
+    if q1:
+        out["butterfly_general_form"] = rate("butterfly")
+    return out
 
 
 def chained_ms(ctx, evk, inp, k, B, L, N, dev, stream, reps):
@@ -766,8 +777,8 @@ def run_reference(args, rank, world):
 
 
 KERNEL_SOURCES = {
-    "ntt": ["ntt.cu", "ntt_kernel.cuh", "ntt_uf.cu", "ntt_ui.cu", "ntt_tf.cu", "ntt_ti.cu", "common.cuh",
-            "internal.h"],
+    "ntt": ["ntt.cu", "ntt_kernel.cuh", "ntt_uf.cu", "ntt_ui.cu", "ntt_tf.cu", "ntt_ti.cu", "ntt_uf1.cu", "ntt_ui1.cu",
+            "ntt_tf1.cu", "ntt_ti1.cu", "common.cuh", "internal.h"],
     "rns": ["rns.cu", "rns.h", "common.cuh", "internal.h"],
 }
 

@@ -452,12 +452,15 @@ int ckks_pull(void *dst, const void *src, size_t bytes, int blocks, void *stream
  *   kind 4  16 x 16 transpose of 64-bit values within each half-warp by
  *           warp shuffles (the exchange between two radix-16 NTT passes)
  *   kind 5  the same transpose through shared memory
- * (kinds 4 and 5 run 16 values per thread and count one operation per
+ *   kind 6  kind 1 with the Shoup product's form for q = 1 (mod 2^32)
+ *   kind 7  kind 0 in that form
+ * (kinds 6 and 7 need q = 1 (mod 2^32), else CKKS_EINVAL before any launch;
+ * kinds 4 and 5 run 16 values per thread and count one operation per
  * value moved: blocks x threads x 16 x iters; q, w, wp are not used)
  * q: odd modulus below 2^62; w, wp: host arrays of ckks_peak_chains() Shoup
  * pairs (w < q). The caller times the launch on `stream` with CUDA events:
  * operations per second = blocks x threads x chains x iters / time
- * (kinds 0-3).
+ * (kinds 0-3, 6, 7).
  * Returns CKKS_EINVAL for bad arguments, CKKS_ECUDA on a launch error. */
 int ckks_peak_chains(void);
 int ckks_peak_int(int kind, uint64_t q, const uint64_t *w, const uint64_t *wp, int blocks, int threads, int iters,
@@ -492,7 +495,13 @@ int ckks_peak_int(int kind, uint64_t q, const uint64_t *w, const uint64_t *wp, i
  * calls (and ckks_check_residues, ckks_evk_verify) that run at the same
  * time on one context, on different streams, share it and may report each
  * other's violations. "nvtx" 1 = NVTX ranges around each stage's launches,
- * for profilers that filter by range. Both default to 0. */
+ * for profilers that filter by range. Both default to 0.
+ * Form of the modular products: when every prime of the context (Q and P)
+ * is 1 (mod 2^32), "q1_forms" 1 (default) lets the kernels compute the
+ * Shoup quotient product and Montgomery's q^-1 and quotient products with
+ * 32-bit multiplies (q = h 2^32 + 1); 0 keeps the general 64-bit forms.
+ * Residues are the same either way; for other primes the value has no
+ * effect. */
 int ckks_tune_set(ckks_context *ctx, const char *key, int value);
 int ckks_tune_get(const ckks_context *ctx, const char *key, int *value);
 

@@ -76,6 +76,43 @@ __device__ __forceinline__ u64 mont_mul(u64 a, u64 b, ModQ m) {
     return redc(mulhi64(a, b), a * b, m);
 }
 
+// REDC for q = 1 (mod 2^32), q = qh 2^32 + 1: q^-1 = 1 - qh 2^32 (mod 2^64),
+// so t = lo q^-1 needs one 32-bit product; with t = t1 2^32 + t0,
+// t q = t1 qh 2^64 + (t0 qh + t1) 2^32 + t0 and the high word of t q is
+// t1 qh + floor((t0 qh + t1) / 2^32): two 32 x 32-bit products instead of a
+// 64 x 64-bit low product and a 64 x 64-bit high product.
+__device__ __forceinline__ u64 redc_q1(u64 hi, u64 lo, u64 q) {
+    const uint32_t qh = (uint32_t)(q >> 32);
+    const u64 t = lo - ((u64)((uint32_t)lo * qh) << 32);
+    const uint32_t t0 = (uint32_t)t, t1 = (uint32_t)(t >> 32);
+    const u64 u = (u64)t1 * qh + (((u64)t0 * qh + t1) >> 32);
+    return hi >= u ? hi - u : hi + q - u;
+}
+
+// The modular products in two forms selected at compile time: Q1 = true for
+// contexts whose primes are all 1 (mod 2^32).
+template <bool Q1>
+__device__ __forceinline__ u64 shoup_lazy_t(u64 x, u64 w, u64 wp, u64 q) {
+    if constexpr (Q1) return shoup_lazy_q1(x, w, wp, (uint32_t)(q >> 32));
+    else return shoup_lazy(x, w, wp, q);
+}
+
+template <bool Q1>
+__device__ __forceinline__ u64 shoup_t(u64 x, u64 w, u64 wp, u64 q) {
+    return reduce2(shoup_lazy_t<Q1>(x, w, wp, q), q);
+}
+
+template <bool Q1>
+__device__ __forceinline__ u64 redc_t(u64 hi, u64 lo, ModQ m) {
+    if constexpr (Q1) return redc_q1(hi, lo, m.q);
+    else return redc(hi, lo, m);
+}
+
+template <bool Q1>
+__device__ __forceinline__ u64 mont_mul_t(u64 a, u64 b, ModQ m) {
+    return redc_t<Q1>(mulhi64(a, b), a * b, m);
+}
+
 // 128-bit accumulator for dot products reduced once by REDC. Adding a product
 // of two values below 2^61 and q keeps hi below q after the conditional
 // subtraction of q 2^64 (which does not change the value mod q).

@@ -110,6 +110,8 @@ int context_build(Context &C, const uint32_t log_n, const uint32_t L, const uint
         for (int j = 0; j < i; ++j)
             if (C.primes[j] == x) return -1;
     }
+    C.primes_q1 = true;
+    for (int i = 0; i < NP; ++i) C.primes_q1 = C.primes_q1 && (C.primes[i] & 0xffffffffull) == 1;
     // BConv sums of products stay below hi < q only if sum of source primes < 2^64
     // (see Acc128); check every digit and the P basis.
     {

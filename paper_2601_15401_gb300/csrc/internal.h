@@ -155,6 +155,12 @@ struct Context {
     // CKKS_ECHECK on a violation); 1 = NVTX ranges per tree node and stage
     int tune_check_residues = 0;
     int tune_nvtx = 0;
+    // every prime (Q and P) is 1 (mod 2^32): the kernels can then take the
+    // cheaper forms of the Shoup product and of REDC (shoup_lazy_q1,
+    // redc_q1); set at creation. tune_q1 = 0 keeps the general forms.
+    bool primes_q1 = false;
+    int tune_q1 = 1;
+    bool q1() const { return primes_q1 && tune_q1 != 0; }
 };
 
 // Records CUDA events around one launch on its stream when the hook is on;

@@ -82,6 +82,12 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
     if (S.mode == ST_SCALE || S.mode == ST_MODDOWN || S.mode == ST_MRS) ops += jobs_d * (double)C.N;
     ProfScope ps(C, fwd ? (cols ? KC_NTT_FWD_COLS : KC_NTT_FWD_BLOCKS) : (cols ? KC_NTT_INV_COLS : KC_NTT_INV_BLOCKS),
                  bytes, st, ops);
+    if (C.q1()) {
+        bool found;
+        const cudaError_t e = fwd ? ntt_dispatch_q1_uniform_fwd(cols, logn, P, J, L, S, G, found)
+                                  : ntt_dispatch_q1_uniform_inv(cols, logn, P, J, L, S, G, found);
+        if (found) return e;
+    }
     return fwd ? ntt_dispatch_uniform_fwd(cols, logn, P, J, L, S, G)
                : ntt_dispatch_uniform_inv(cols, logn, P, J, L, S, G);
 }
@@ -101,6 +107,12 @@ cudaError_t launch_ntt_phase_table(const Context &C, bool fwd, bool cols, const 
     count_kernel(C);
     ProfScope ps(C, fwd ? (cols ? KC_NTT_FWD_COLS : KC_NTT_FWD_BLOCKS) : (cols ? KC_NTT_INV_COLS : KC_NTT_INV_BLOCKS),
                  alg_bytes, st, ops);
+    if (C.q1()) {
+        bool found;
+        const cudaError_t e = fwd ? ntt_dispatch_q1_table_fwd(cols, logn, P, jobs, n_jobs, L, S, G, found)
+                                  : ntt_dispatch_q1_table_inv(cols, logn, P, jobs, n_jobs, L, S, G, found);
+        if (found) return e;
+    }
     return fwd ? ntt_dispatch_table_fwd(cols, logn, P, jobs, n_jobs, L, S, G)
                : ntt_dispatch_table_inv(cols, logn, P, jobs, n_jobs, L, S, G);
 }

@@ -48,20 +48,22 @@ namespace ckks {
 // ---------------------------------------------------------------------------
 // butterflies
 // ---------------------------------------------------------------------------
+template <bool Q1>
 __device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
     u64 q2 = q << 1;
     u64 x = X >= q2 ? X - q2 : X;
-    u64 t = shoup_lazy(Y, w.x, w.y, q);
+    u64 t = shoup_lazy_t<Q1>(Y, w.x, w.y, q);
     X = x + t;
     Y = x - t + q2;
 }
 
+template <bool Q1>
 __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
     u64 q2 = q << 1;
     u64 s = X + Y;
     s = s >= q2 ? s - q2 : s;
     u64 d = X - Y + q2;
-    Y = shoup_lazy(d, w.x, w.y, q);
+    Y = shoup_lazy_t<Q1>(d, w.x, w.y, q);
     X = s;
 }
 
@@ -196,7 +198,7 @@ __device__ __forceinline__ StoreCtx make_store(const StoreSpec &S, const NttJob 
     return c;
 }
 
-template <int LM>
+template <int LM, bool Q1>
 __device__ __forceinline__ u64 load_elem(const LoadCtx &c, int e) {
     const u64 q = c.m.q;
     const int mode = LM >= 0 ? LM : c.mode;
@@ -206,22 +208,23 @@ __device__ __forceinline__ u64 load_elem(const LoadCtx &c, int e) {
     case LD_EQ17: {
         // sum_t g_t T_t (mod q); with the self term: g_self a - sum
         u64 s = 0;
-        for (int t = 0; t < c.mu; ++t) s = add_mod(s, shoup(c.b[(i64)t * c.N + e], c.g[t].w, c.g[t].wp, q), q);
-        if (c.with_self) s = sub_mod(shoup(c.a[e], c.g[c.mu].w, c.g[c.mu].wp, q), s, q);
+        for (int t = 0; t < c.mu; ++t)
+            s = add_mod(s, shoup_t<Q1>(c.b[(i64)t * c.N + e], c.g[t].w, c.g[t].wp, q), q);
+        if (c.with_self) s = sub_mod(shoup_t<Q1>(c.a[e], c.g[c.mu].w, c.g[c.mu].wp, q), s, q);
         return s;
     }
     case LD_BCONVK: {
         Acc128Lazy acc;  // sum of the P primes < 2^64 (context check)
         acc.zero();
         for (int i = 0; i < c.K; ++i) acc.mac(c.b[(i64)i * c.N + e], c.cK[i]);
-        return redc(acc.hi, acc.lo, c.m);
+        return redc_t<Q1>(acc.hi, acc.lo, c.m);
     }
     default:
         return c.a[e];
     }
 }
 
-template <int SM>
+template <int SM, bool Q1>
 __device__ __forceinline__ void store_elem(const StoreCtx &c, int e, u64 v, bool fwd) {
     const u64 q = c.m.q;
     const int mode = SM >= 0 ? SM : c.mode;
@@ -230,20 +233,20 @@ __device__ __forceinline__ void store_elem(const StoreCtx &c, int e, u64 v, bool
         c.dst[e] = v;
         break;
     case ST_SCALE:
-        c.dst[e] = shoup(v, c.c.w, c.c.wp, q);
+        c.dst[e] = shoup_t<Q1>(v, c.c.w, c.c.wp, q);
         break;
     case ST_MODDOWN: {
         // c* = v N^-1 - sum_i z_i [p_i^-1 R]_q  (Eq. 5 with Eq. 11 / 12)
-        u64 x = shoup(v, c.c.w, c.c.wp, q);
+        u64 x = shoup_t<Q1>(v, c.c.w, c.c.wp, q);
         Acc128Lazy acc;  // sum of the P primes < 2^64 (context check)
         acc.zero();
         for (int i = 0; i < c.K; ++i) acc.mac(c.aux[(i64)i * c.N + e], c.cK[i]);
-        c.dst[e] = sub_mod(x, redc(acc.hi, acc.lo, c.m), q);
+        c.dst[e] = sub_mod(x, redc_t<Q1>(acc.hi, acc.lo, c.m), q);
         break;
     }
     case ST_MRS:
         // Algorithm 1, last step: A' = g^{mu,L-1} A - B
-        c.dst[e] = sub_mod(shoup(c.aux[e], c.c.w, c.c.wp, q), fwd ? reduce4(v, q) : reduce2(v, q), q);
+        c.dst[e] = sub_mod(shoup_t<Q1>(c.aux[e], c.c.w, c.c.wp, q), fwd ? reduce4(v, q) : reduce2(v, q), q);
         break;
     case ST_ADDSUB:
         c.dst[e] = sub_mod(add_mod(c.aux[e], c.aux2[e], q), fwd ? reduce4(v, q) : reduce2(v, q), q);
@@ -257,7 +260,7 @@ __device__ __forceinline__ void store_elem(const StoreCtx &c, int e, u64 v, bool
 // One pass of R stages starting at local stage E0 on every point set of the
 // tile. GIN / GOUT: the pass reads / writes global memory (fused load /
 // store) instead of shared memory.
-template <int LOGN, int R, int E0, bool FWD, bool COLS, bool GIN, bool GOUT, int LM, int SM>
+template <int LOGN, int R, int E0, bool FWD, bool COLS, bool GIN, bool GOUT, int LM, int SM, bool Q1>
 __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay, const ulonglong2 *tw, int tw_b0,
                                          int tw_bmul, u64 q, const LoadCtx &lc, const StoreCtx &sc, int t0,
                                          int log_n2) {
@@ -279,7 +282,7 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
             const int pt = base + k * t_min;
             if (GIN) {
                 const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
-                x[k] = load_elem<LM>(lc, e);
+                x[k] = load_elem<LM, Q1>(lc, e);
             } else {
                 x[k] = sm[lay.off(sp, pt)];
             }
@@ -294,7 +297,7 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
                 for (int k = 0; k < EL; ++k) {
                     if ((k & h) == 0) {
                         const int i = (g << ep) + (k >> (R - ep));
-                        ct_bfly(x[k], x[k + h], tw[m * twb + i], q);
+                        ct_bfly<Q1>(x[k], x[k + h], tw[m * twb + i], q);
                     }
                 }
             }
@@ -307,7 +310,7 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
                 for (int k = 0; k < EL; ++k) {
                     if ((k & h) == 0) {
                         const int i = (g << ep) + (k >> (R - ep));
-                        gs_bfly(x[k], x[k + h], tw[m * twb + i], q);
+                        gs_bfly<Q1>(x[k], x[k + h], tw[m * twb + i], q);
                     }
                 }
             }
@@ -317,7 +320,7 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
             const int pt = base + k * t_min;
             if (GOUT) {
                 const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
-                store_elem<SM>(sc, e, x[k], FWD);
+                store_elem<SM, Q1>(sc, e, x[k], FWD);
             } else {
                 sm[lay.off(sp, pt)] = x[k];
             }
@@ -339,7 +342,7 @@ struct PassAccess {
     static constexpr bool direct_in = direct && CKKS_NTT_DIRECT_IN;
 };
 
-template <int LOGN, bool FWD, bool COLS, int LM, int SM, int I>
+template <int LOGN, bool FWD, bool COLS, int LM, int SM, bool Q1, int I>
 __device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS, LOGN> &lay, const ulonglong2 *tw, int tw_b0,
                                            int tw_bmul, u64 q, const LoadCtx &lc, const StoreCtx &sc, int t0,
                                            int log_n2) {
@@ -349,15 +352,15 @@ __device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS, LOGN> &la
         constexpr bool first = I == 0, last = I == NP - 1;
         constexpr bool gin = first && PassAccess<LOGN, COLS, PP>::direct_in;
         constexpr bool gout = last && PassAccess<LOGN, COLS, PP>::direct;
-        run_pass<LOGN, Pass<LOGN, PP>::len, Pass<LOGN, PP>::start, FWD, COLS, gin, gout, LM, SM>(
+        run_pass<LOGN, Pass<LOGN, PP>::len, Pass<LOGN, PP>::start, FWD, COLS, gin, gout, LM, SM, Q1>(
             sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
         if (!last || !gout) __syncthreads();
-        run_passes<LOGN, FWD, COLS, LM, SM, I + 1>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
+        run_passes<LOGN, FWD, COLS, LM, SM, Q1, I + 1>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
     }
 }
 
 // One tile (CTA) of one limb: tile index `tile` of the phase.
-template <int LOGN, bool FWD, bool COLS, int LM, int SM>
+template <int LOGN, bool FWD, bool COLS, int LM, int SM, bool Q1>
 __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulonglong2 *tw, u64 q,
                                            const LoadCtx &lc, const StoreCtx &sc, int tile) {
     constexpr int n = 1 << LOGN;
@@ -387,7 +390,7 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
                     int sp, k, e;
                     if (COLS) { k = idx >> lsub; sp = idx & (n_sub - 1); e = t0 + sp + (k << P.log_n2); }
                     else { sp = idx >> LOGN; k = idx & (n - 1); e = ((t0 + sp) << LOGN) + k; }
-                    v[u] = load_elem<LM>(lc, e);
+                    v[u] = load_elem<LM, Q1>(lc, e);
                 }
             }
 #pragma unroll
@@ -403,14 +406,14 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
         }
         __syncthreads();
     }
-    run_passes<LOGN, FWD, COLS, LM, SM, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
+    run_passes<LOGN, FWD, COLS, LM, SM, Q1, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
     if (!gout) {
         // shared -> global with the fused store (coalesced)
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             int sp, k, e;
             if (COLS) { k = idx >> lsub; sp = idx & (n_sub - 1); e = t0 + sp + (k << P.log_n2); }
             else { sp = idx >> LOGN; k = idx & (n - 1); e = ((t0 + sp) << LOGN) + k; }
-            store_elem<SM>(sc, e, sm[lay.off(sp, k)], FWD);
+            store_elem<SM, Q1>(sc, e, sm[lay.off(sp, k)], FWD);
         }
     }
 }
@@ -419,7 +422,7 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
 // the phase kernels: grid (tiles, limbs) for uniform launches, one
 // flattened dimension (limb * tiles + tile) for table launches
 // ---------------------------------------------------------------------------
-template <int LOGN, bool FWD, bool COLS, int LM, int SM, int MINB>
+template <int LOGN, bool FWD, bool COLS, int LM, int SM, int MINB, bool Q1>
 __global__ void __launch_bounds__(256, MINB) ntt_phase_kernel(NttPhase P, LimbJobs J, LoadSpec L, StoreSpec S) {
     extern __shared__ u64 sm[];
     int b, p, l;
@@ -429,10 +432,10 @@ __global__ void __launch_bounds__(256, MINB) ntt_phase_kernel(NttPhase P, LimbJo
     const ulonglong2 *tw = (FWD ? P.tw_fwd : P.tw_inv) + (i64)prime * P.N;
     const LoadCtx lc = make_load(L, J, P.N, b, p, l, prime, m);
     const StoreCtx sc = make_store(S, J, P.N, b, p, l, prime, m);
-    phase_tile<LOGN, FWD, COLS, LM, SM>(sm, P, tw, m.q, lc, sc, blockIdx.x);
+    phase_tile<LOGN, FWD, COLS, LM, SM, Q1>(sm, P, tw, m.q, lc, sc, blockIdx.x);
 }
 
-template <int LOGN, bool FWD, bool COLS, int LM, int SM, int MINB>
+template <int LOGN, bool FWD, bool COLS, int LM, int SM, int MINB, bool Q1>
 __global__ void __launch_bounds__(256, MINB) ntt_phase_table_kernel(NttPhase P, const NttJob *jobs, int tiles,
                                                                     LoadSpec L, StoreSpec S) {
     extern __shared__ u64 sm[];
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(256, MINB) ntt_phase_table_kernel(NttPhase P, 
     const ulonglong2 *tw = (FWD ? P.tw_fwd : P.tw_inv) + (i64)j.prime * P.N;
     const LoadCtx lc = make_load(L, j, P.N, m);
     const StoreCtx sc = make_store(S, j, P.N, m);
-    phase_tile<LOGN, FWD, COLS, LM, SM>(sm, P, tw, m.q, lc, sc, tile);
+    phase_tile<LOGN, FWD, COLS, LM, SM, Q1>(sm, P, tw, m.q, lc, sc, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -472,10 +475,10 @@ static inline cudaError_t allow_smem(K kern, size_t smem) {
     return cudaSuccess;
 }
 
-template <int LOGN, bool FWD, bool COLS, int LM, int SM, int MINB>
+template <int LOGN, bool FWD, bool COLS, int LM, int SM, int MINB, bool Q1>
 static inline cudaError_t launch_uniform(const NttPhase &P, const LimbJobs &J, const LoadSpec &L,
                                          const StoreSpec &S, const PhaseLaunch &G) {
-    auto kern = ntt_phase_kernel<LOGN, FWD, COLS, LM, SM, MINB>;
+    auto kern = ntt_phase_kernel<LOGN, FWD, COLS, LM, SM, MINB, Q1>;
     cudaError_t e = allow_smem(kern, G.smem);
     if (e != cudaSuccess) return e;
     dim3 grid(G.tiles, J.n_batch * J.n_polys * J.n_limbs);
@@ -483,10 +486,10 @@ static inline cudaError_t launch_uniform(const NttPhase &P, const LimbJobs &J, c
     return cudaGetLastError();
 }
 
-template <int LOGN, bool FWD, bool COLS, int LM, int SM, int MINB>
+template <int LOGN, bool FWD, bool COLS, int LM, int SM, int MINB, bool Q1>
 static inline cudaError_t launch_table(const NttPhase &P, const NttJob *jobs, int n_jobs, const LoadSpec &L,
                                        const StoreSpec &S, const PhaseLaunch &G) {
-    auto kern = ntt_phase_table_kernel<LOGN, FWD, COLS, LM, SM, MINB>;
+    auto kern = ntt_phase_table_kernel<LOGN, FWD, COLS, LM, SM, MINB, Q1>;
     cudaError_t e = allow_smem(kern, G.smem);
     if (e != cudaSuccess) return e;
     const long long blocks = (long long)n_jobs * G.tiles;
@@ -497,47 +500,60 @@ static inline cudaError_t launch_table(const NttPhase &P, const NttJob *jobs, in
 }
 
 // Dispatch of one direction (FWD) and job source (TABLE) over the phase
-// geometry (cols, log2 n) and the modes: a specialised kernel for the mode
-// combinations of the hot path at n = 128 / 256 (N = 2^14 .. 2^16), the
-// run-time-mode kernel otherwise.
-template <bool FWD, bool TABLE>
-static inline cudaError_t dispatch_phase(bool cols, int logn, const NttPhase &P, const LimbJobs *J,
-                                         const NttJob *jobs, int n_jobs, const LoadSpec &L, const StoreSpec &S,
-                                         const PhaseLaunch &G) {
-#define CKKS_LAUNCH(LG, CO, LMv, SMv, MB)                                                  \
-    do {                                                                                   \
-        if constexpr (TABLE) return launch_table<LG, FWD, CO, LMv, SMv, MB>(P, jobs, n_jobs, L, S, G); \
-        else return launch_uniform<LG, FWD, CO, LMv, SMv, MB>(P, *J, L, S, G);             \
+// geometry (cols, log2 n) and the modes. dispatch_fast launches the
+// specialised kernel for the mode combinations of the hot path at n = 128 /
+// 256 (N = 2^14 .. 2^16), with the modular products in the form Q1 selects,
+// and sets `found`; dispatch_generic launches the run-time-mode kernel (the
+// general products, valid for every prime).
+#define CKKS_LAUNCH(LG, CO, LMv, SMv, MB, Q)                                                         \
+    do {                                                                                             \
+        if constexpr (TABLE) return launch_table<LG, FWD, CO, LMv, SMv, MB, Q>(P, jobs, n_jobs, L, S, G); \
+        else return launch_uniform<LG, FWD, CO, LMv, SMv, MB, Q>(P, *J, L, S, G);                    \
     } while (0)
+
+template <bool FWD, bool TABLE, bool Q1>
+static inline cudaError_t dispatch_fast(bool cols, int logn, const NttPhase &P, const LimbJobs *J,
+                                        const NttJob *jobs, int n_jobs, const LoadSpec &L, const StoreSpec &S,
+                                        const PhaseLaunch &G, bool &found) {
+    found = true;
     // specialised: the phase that fuses a mode has the plain mode on its other side
 #define CKKS_FAST(LG)                                                                              \
     if (logn == LG) {                                                                              \
         if constexpr (FWD) {                                                                       \
             if (cols && S.mode == ST_LAZY) {                                                       \
-                if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB); \
-                if (L.mode == LD_EQ17) CKKS_LAUNCH(LG, true, LD_EQ17, ST_LAZY, CKKS_NTT_EQ17_MINB);   \
+                if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB, Q1); \
+                if (L.mode == LD_EQ17) CKKS_LAUNCH(LG, true, LD_EQ17, ST_LAZY, CKKS_NTT_EQ17_MINB, Q1);   \
             }                                                                                      \
             if (!cols && L.mode == LD_PLAIN) {                                                     \
-                if (S.mode == ST_REDUCE) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_REDUCE, CKKS_NTT_FAST_MINB); \
-                if (S.mode == ST_MRS) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_MRS, CKKS_NTT_FAST_MINB);   \
+                if (S.mode == ST_REDUCE) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_REDUCE, CKKS_NTT_FAST_MINB, Q1); \
+                if (S.mode == ST_MRS) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_MRS, CKKS_NTT_FAST_MINB, Q1);   \
             }                                                                                      \
         } else {                                                                                   \
             if (!cols && S.mode == ST_LAZY) {                                                      \
-                if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB); \
-                if (L.mode == LD_ADD) CKKS_LAUNCH(LG, false, LD_ADD, ST_LAZY, CKKS_NTT_FAST_MINB);    \
+                if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, false, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB, Q1); \
+                if (L.mode == LD_ADD) CKKS_LAUNCH(LG, false, LD_ADD, ST_LAZY, CKKS_NTT_FAST_MINB, Q1);    \
             }                                                                                      \
             if (cols && L.mode == LD_PLAIN) {                                                      \
-                if (S.mode == ST_SCALE) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_SCALE, CKKS_NTT_FAST_MINB); \
-                if (S.mode == ST_MODDOWN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_MODDOWN, CKKS_NTT_FAST_MINB); \
+                if (S.mode == ST_SCALE) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_SCALE, CKKS_NTT_FAST_MINB, Q1); \
+                if (S.mode == ST_MODDOWN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_MODDOWN, CKKS_NTT_FAST_MINB, Q1); \
             }                                                                                      \
         }                                                                                          \
     }
     CKKS_FAST(7)
     CKKS_FAST(8)
+#undef CKKS_FAST
+    found = false;
+    return cudaSuccess;
+}
+
+template <bool FWD, bool TABLE>
+static inline cudaError_t dispatch_generic(bool cols, int logn, const NttPhase &P, const LimbJobs *J,
+                                           const NttJob *jobs, int n_jobs, const LoadSpec &L, const StoreSpec &S,
+                                           const PhaseLaunch &G) {
 #define CKKS_GENERIC(LG)                                                          \
     case LG:                                                                      \
-        if (cols) CKKS_LAUNCH(LG, true, -1, -1, CKKS_NTT_MINB);                   \
-        CKKS_LAUNCH(LG, false, -1, -1, CKKS_NTT_MINB)
+        if (cols) CKKS_LAUNCH(LG, true, -1, -1, CKKS_NTT_MINB, false);            \
+        CKKS_LAUNCH(LG, false, -1, -1, CKKS_NTT_MINB, false)
     switch (logn) {
         CKKS_GENERIC(1);
         CKKS_GENERIC(2);
@@ -551,11 +567,32 @@ static inline cudaError_t dispatch_phase(bool cols, int logn, const NttPhase &P,
         return cudaErrorInvalidValue;
     }
 #undef CKKS_GENERIC
-#undef CKKS_FAST
+}
 #undef CKKS_LAUNCH
+
+// general products: the specialised kernel if one matches, else the generic one
+template <bool FWD, bool TABLE>
+static inline cudaError_t dispatch_phase(bool cols, int logn, const NttPhase &P, const LimbJobs *J,
+                                         const NttJob *jobs, int n_jobs, const LoadSpec &L, const StoreSpec &S,
+                                         const PhaseLaunch &G) {
+    bool found;
+    const cudaError_t e = dispatch_fast<FWD, TABLE, false>(cols, logn, P, J, jobs, n_jobs, L, S, G, found);
+    if (found) return e;
+    return dispatch_generic<FWD, TABLE>(cols, logn, P, J, jobs, n_jobs, L, S, G);
 }
 
-// ntt_uf.cu / ntt_ui.cu / ntt_tf.cu / ntt_ti.cu
+// ntt_uf.cu / ntt_ui.cu / ntt_tf.cu / ntt_ti.cu: general products;
+// ntt_uf1.cu / ntt_ui1.cu / ntt_tf1.cu / ntt_ti1.cu: the specialised kernels
+// with the products for primes = 1 (mod 2^32) (`found` false when none
+// matches: the caller then takes the general dispatch)
+cudaError_t ntt_dispatch_q1_uniform_fwd(bool cols, int logn, const NttPhase &P, const LimbJobs &J,
+                                        const LoadSpec &L, const StoreSpec &S, const PhaseLaunch &G, bool &found);
+cudaError_t ntt_dispatch_q1_uniform_inv(bool cols, int logn, const NttPhase &P, const LimbJobs &J,
+                                        const LoadSpec &L, const StoreSpec &S, const PhaseLaunch &G, bool &found);
+cudaError_t ntt_dispatch_q1_table_fwd(bool cols, int logn, const NttPhase &P, const NttJob *jobs, int n_jobs,
+                                      const LoadSpec &L, const StoreSpec &S, const PhaseLaunch &G, bool &found);
+cudaError_t ntt_dispatch_q1_table_inv(bool cols, int logn, const NttPhase &P, const NttJob *jobs, int n_jobs,
+                                      const LoadSpec &L, const StoreSpec &S, const PhaseLaunch &G, bool &found);
 cudaError_t ntt_dispatch_uniform_fwd(bool cols, int logn, const NttPhase &P, const LimbJobs &J, const LoadSpec &L,
                                      const StoreSpec &S, const PhaseLaunch &G);
 cudaError_t ntt_dispatch_uniform_inv(bool cols, int logn, const NttPhase &P, const LimbJobs &J, const LoadSpec &L,

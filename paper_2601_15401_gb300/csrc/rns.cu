@@ -50,7 +50,7 @@ struct TensorTableView {
 // MAXT bounds every tuple size involved (children and output), so the
 // unrolled, predicated product loops stay short for small nodes.
 // r = limb * N + coefficient, j = the limb's prime.
-template <int MAXT, class V>
+template <int MAXT, bool Q1, class V>
 __device__ __forceinline__ void tensor_coeff(const V &v, i64 r, int j, const ModQ m, const u64 *rpow) {
     const u64 q = m.q;
     u64 cur[MAXT];
@@ -97,7 +97,7 @@ __device__ __forceinline__ void tensor_coeff(const V &v, i64 r, int j, const Mod
                 }
             }
 #pragma unroll
-            for (int t = 0; t < MAXT; ++t) nxt[t] = t < ncur + 1 ? redc(acc[t].hi, acc[t].lo, m) : 0ull;
+            for (int t = 0; t < MAXT; ++t) nxt[t] = t < ncur + 1 ? redc_t<Q1>(acc[t].hi, acc[t].lo, m) : 0ull;
         } else {
 #pragma unroll
             for (int t = 0; t < MAXT; ++t) {
@@ -107,7 +107,7 @@ __device__ __forceinline__ void tensor_coeff(const V &v, i64 r, int j, const Mod
                 for (int a = 0; a <= t; ++a) {
                     if (a < ncur && t - a < ny) acc.mac(cur[a], y[t - a], q);
                 }
-                nxt[t] = t < ncur + ny - 1 ? redc(acc.hi, acc.lo, m) : 0ull;
+                nxt[t] = t < ncur + ny - 1 ? redc_t<Q1>(acc.hi, acc.lo, m) : 0ull;
             }
         }
         ncur = ncur + ny - 1;
@@ -119,20 +119,20 @@ __device__ __forceinline__ void tensor_coeff(const V &v, i64 r, int j, const Mod
     const i64 ds = v.dstride();
 #pragma unroll
     for (int t = 0; t < MAXT; ++t)
-        if (t < ncur) dst[(i64)t * ds] = mont_mul(cur[t], fix, m);
+        if (t < ncur) dst[(i64)t * ds] = mont_mul_t<Q1>(cur[t], fix, m);
 }
 
-template <int MAXT>
+template <int MAXT, bool Q1>
 __global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
     const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;  // limb * N + coefficient
     if (r >= (i64)A.level * A.N) return;
     const int j = (int)(r >> A.log_n);
-    tensor_coeff<MAXT>(TensorUniformView{A, (int)blockIdx.y}, r, j, A.mods[j], A.rpow);
+    tensor_coeff<MAXT, Q1>(TensorUniformView{A, (int)blockIdx.y}, r, j, A.mods[j], A.rpow);
 }
 
 // Table launch: blockIdx.y = tree node; the node's entry is staged in shared
 // memory (it is indexed by child at run time).
-template <int MAXT>
+template <int MAXT, bool Q1>
 __global__ void __launch_bounds__(kThreads) tensor_table_kernel(const TensorJob *jobs, int N, int log_n,
                                                                 const ModQ *mods, const u64 *rpow) {
     __shared__ TensorJob J;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) tensor_table_kernel(const TensorJob 
     const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (i64)J.level * N) return;
     const int j = (int)(r >> log_n);
-    tensor_coeff<MAXT>(TensorTableView{J}, r, j, mods[j], rpow);
+    tensor_coeff<MAXT, Q1>(TensorTableView{J}, r, j, mods[j], rpow);
 }
 
 // 64 x 64 -> 128-bit products per coefficient of a node's tensor product
@@ -167,6 +167,27 @@ double tensor_products_per_coeff(const int *polys, int m) {
     return ops + ncur;  // the final R^m correction
 }
 
+template <bool Q1>
+static void launch_tensor_sized(int maxt, dim3 blocks, const TensorArgs &A, cudaStream_t st) {
+    if (maxt <= 3) tensor_kernel<3, Q1><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 4) tensor_kernel<4, Q1><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 5) tensor_kernel<5, Q1><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 7) tensor_kernel<7, Q1><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 9) tensor_kernel<9, Q1><<<blocks, kThreads, 0, st>>>(A);
+    else tensor_kernel<CKKS_MAX_TUPLE, Q1><<<blocks, kThreads, 0, st>>>(A);
+}
+
+template <bool Q1>
+static void launch_tensor_table_sized(const Context &C, int maxt, dim3 blocks, const TensorJob *jobs,
+                                      cudaStream_t st) {
+    if (maxt <= 3) tensor_table_kernel<3, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else if (maxt <= 4) tensor_table_kernel<4, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else if (maxt <= 5) tensor_table_kernel<5, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else if (maxt <= 7) tensor_table_kernel<7, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else if (maxt <= 9) tensor_table_kernel<9, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    else tensor_table_kernel<CKKS_MAX_TUPLE, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+}
+
 cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t st) {
     TensorArgs A = Ain;
     A.log_n = C.log_n;
@@ -182,12 +203,8 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t 
     const double coeffs = (double)A.n_batch * A.level * A.N;
     ProfScope ps(C, KC_TENSOR, (double)(in_polys + out_polys) * coeffs * sizeof(u64), st,
                  coeffs * tensor_products_per_coeff(A.child_polys, A.m));
-    if (maxt <= 3) tensor_kernel<3><<<blocks, kThreads, 0, st>>>(A);
-    else if (maxt <= 4) tensor_kernel<4><<<blocks, kThreads, 0, st>>>(A);
-    else if (maxt <= 5) tensor_kernel<5><<<blocks, kThreads, 0, st>>>(A);
-    else if (maxt <= 7) tensor_kernel<7><<<blocks, kThreads, 0, st>>>(A);
-    else if (maxt <= 9) tensor_kernel<9><<<blocks, kThreads, 0, st>>>(A);
-    else tensor_kernel<CKKS_MAX_TUPLE><<<blocks, kThreads, 0, st>>>(A);
+    if (C.q1()) launch_tensor_sized<true>(maxt, blocks, A, st);
+    else launch_tensor_sized<false>(maxt, blocks, A, st);
     return cudaGetLastError();
 }
 
@@ -198,12 +215,8 @@ cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_j
     dim3 blocks((unsigned)(((i64)max_level * C.N + kThreads - 1) / kThreads), (unsigned)n_jobs);
     count_kernel(C);
     ProfScope ps(C, KC_TENSOR, bytes, st, ops);
-    if (maxt <= 3) tensor_table_kernel<3><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else if (maxt <= 4) tensor_table_kernel<4><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else if (maxt <= 5) tensor_table_kernel<5><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else if (maxt <= 7) tensor_table_kernel<7><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else if (maxt <= 9) tensor_table_kernel<9><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else tensor_table_kernel<CKKS_MAX_TUPLE><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+    if (C.q1()) launch_tensor_table_sized<true>(C, maxt, blocks, jobs, st);
+    else launch_tensor_table_sized<false>(C, maxt, blocks, jobs, st);
     return cudaGetLastError();
 }
 
@@ -250,7 +263,7 @@ __device__ __forceinline__ void store_span(u64 *p, const u64 (&v)[V]) {
 // One CTA: the constants of (level, digit) staged in shared memory, then one
 // coefficient per thread. y: limb 0 of the prescaled d_t; dst: slot 0 of the
 // (t, digit) ModUp output.
-template <int AMAX>
+template <int AMAX, bool Q1>
 __device__ __forceinline__ void bconv_block(const u64 *ctab, const u64 *y0, u64 *dst0, int level, int beta,
                                             int alpha, int L, int K, int n_primes, int N, const ModQ *mods, u64 *cs) {
     const int d0 = beta * alpha;
@@ -298,31 +311,50 @@ __device__ __forceinline__ void bconv_block(const u64 *ctab, const u64 *y0, u64 
             }
         u64 r[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) r[v] = redc(acc[v].hi, acc[v].lo, m);
+        for (int v = 0; v < V; ++v) r[v] = redc_t<Q1>(acc[v].hi, acc[v].lo, m);
         store_span<V>(dst + (i64)slot * N, r);
     }
 }
 
-template <int AMAX>
+template <int AMAX, bool Q1>
 __global__ void __launch_bounds__(1024) bconv_kernel(BconvArgs A) {
     extern __shared__ u64 cs[];  // [alpha][n_targets] Montgomery constants
     const int job = blockIdx.y;
     const int b = blockIdx.z;
     const int t = job / A.n_digits;
     const int beta = job % A.n_digits;
-    bconv_block<AMAX>(A.consts + (i64)beta * A.alpha * A.n_primes,
+    bconv_block<AMAX, Q1>(A.consts + (i64)beta * A.alpha * A.n_primes,
                       A.y.ptr + (i64)b * A.y.bstride + (i64)t * A.y.pstride,
                       A.ext.ptr + (i64)b * A.ext.bstride + (i64)(t * A.n_digits + beta) * A.ext.pstride, A.level, beta,
                       A.alpha, A.L, A.K, A.n_primes, A.N, A.mods, cs);
 }
 
 // Table launch: blockIdx.y = (product, d_t, digit) entry.
-template <int AMAX>
+template <int AMAX, bool Q1>
 __global__ void __launch_bounds__(1024) bconv_table_kernel(const BconvJob *jobs, int alpha, int L, int K,
                                                            int n_primes, int N, const ModQ *mods) {
     extern __shared__ u64 cs[];
     const BconvJob J = jobs[blockIdx.y];
-    bconv_block<AMAX>(J.consts, J.y, J.ext, J.level, J.beta, alpha, L, K, n_primes, N, mods, cs);
+    bconv_block<AMAX, Q1>(J.consts, J.y, J.ext, J.level, J.beta, alpha, L, K, n_primes, N, mods, cs);
+}
+
+template <bool Q1>
+static void launch_bconv_sized(int alpha, dim3 grid, int thr, size_t smem, const BconvArgs &A, cudaStream_t st) {
+    if (alpha <= 4) bconv_kernel<4, Q1><<<grid, thr, smem, st>>>(A);
+    else if (alpha <= 8) bconv_kernel<8, Q1><<<grid, thr, smem, st>>>(A);
+    else if (alpha <= 12) bconv_kernel<12, Q1><<<grid, thr, smem, st>>>(A);
+    else bconv_kernel<16, Q1><<<grid, thr, smem, st>>>(A);
+}
+
+template <bool Q1>
+static void launch_bconv_table_sized(const Context &C, dim3 grid, int thr, size_t smem, const BconvJob *jobs,
+                                     cudaStream_t st) {
+    const int np = C.L + C.K;
+    if (C.alpha <= 4) bconv_table_kernel<4, Q1><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else if (C.alpha <= 8) bconv_table_kernel<8, Q1><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else if (C.alpha <= 12)
+        bconv_table_kernel<12, Q1><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    else bconv_table_kernel<16, Q1><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
 }
 
 cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) {
@@ -341,10 +373,8 @@ cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st) 
     }
     macs *= (double)A.n_t * A.n_batch * A.N;
     ProfScope ps(C, KC_BCONV, ((double)A.n_t * A.level + limbs_out) * A.n_batch * A.N * sizeof(u64), st, macs);
-    if (A.alpha <= 4) bconv_kernel<4><<<grid, thr, smem, st>>>(A);
-    else if (A.alpha <= 8) bconv_kernel<8><<<grid, thr, smem, st>>>(A);
-    else if (A.alpha <= 12) bconv_kernel<12><<<grid, thr, smem, st>>>(A);
-    else bconv_kernel<16><<<grid, thr, smem, st>>>(A);
+    if (C.q1()) launch_bconv_sized<true>(A.alpha, grid, thr, smem, A, st);
+    else launch_bconv_sized<false>(A.alpha, grid, thr, smem, A, st);
     return cudaGetLastError();
 }
 
@@ -358,11 +388,8 @@ cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_job
     count_kernel(C);
     count_op(C, OP_BCONV, (unsigned long long)n_jobs);
     ProfScope ps(C, KC_BCONV, bytes, st, macs);
-    const int np = C.L + C.K;
-    if (C.alpha <= 4) bconv_table_kernel<4><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
-    else if (C.alpha <= 8) bconv_table_kernel<8><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
-    else if (C.alpha <= 12) bconv_table_kernel<12><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
-    else bconv_table_kernel<16><<<grid, thr, smem, st>>>(jobs, C.alpha, C.L, C.K, np, C.N, C.d_mods);
+    if (C.q1()) launch_bconv_table_sized<true>(C, grid, thr, smem, jobs, st);
+    else launch_bconv_table_sized<false>(C, grid, thr, smem, jobs, st);
     return cudaGetLastError();
 }
 
@@ -378,7 +405,7 @@ cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_job
 // V coefficients of accumulator limb x of one product: dsrc / esrc point at
 // limb x, coefficient e of the D tuple / the first ModUp output; krow at the
 // prime's row, coefficient e, of the first key.
-template <int V>
+template <int V, bool Q1>
 __device__ __forceinline__ void mac_span(const u64 *dsrc, i64 dstride, const u64 *esrc, i64 estride, int n, int nd,
                                          int my_digit, const u64 *krow, i64 key_pstride, int key_digits, const ModQ m,
                                          u64 *dst, i64 astride) {
@@ -407,13 +434,14 @@ __device__ __forceinline__ void mac_span(const u64 *dsrc, i64 dstride, const u64
     u64 r0[V], r1[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        r0[v] = redc(a0[v].hi, a0[v].lo, m);
-        r1[v] = redc(a1[v].hi, a1[v].lo, m);
+        r0[v] = redc_t<Q1>(a0[v].hi, a0[v].lo, m);
+        r1[v] = redc_t<Q1>(a1[v].hi, a1[v].lo, m);
     }
     store_span<V>(dst, r0);
     store_span<V>(dst + astride, r1);
 }
 
+template <bool Q1>
 __global__ void __launch_bounds__(1024) mac_kernel(MacArgs A) {
     constexpr int V = CKKS_MAC_VEC;
     const int chunks = (A.N + blockDim.x * V - 1) / (blockDim.x * V);
@@ -429,7 +457,7 @@ __global__ void __launch_bounds__(1024) mac_kernel(MacArgs A) {
     const bool isq = x < A.level;
     const int prime = isq ? x : A.L + (x - A.level);
     const i64 off = (i64)x * A.N + e;
-    mac_span<V>(A.d.ptr + (i64)b * A.d.bstride + off, A.d.pstride, A.ext.ptr + (i64)b * A.ext.bstride + off,
+    mac_span<V, Q1>(A.d.ptr + (i64)b * A.d.bstride + off, A.d.pstride, A.ext.ptr + (i64)b * A.ext.bstride + off,
                 A.ext.pstride, A.n, A.n_digits, isq ? x / A.alpha : -1, A.keys + (i64)prime * A.N + e, A.key_pstride,
                 A.key_digits, A.mods[prime], A.acc.ptr + (i64)b * A.acc.bstride + off, A.acc.pstride);
 }
@@ -446,13 +474,15 @@ cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
     double bytes = ((terms + 2.0) * A.n_batch + 2.0 * terms) * limbs * A.N * sizeof(u64);
     const double macs = 2.0 * terms * limbs * A.n_batch * A.N;
     ProfScope ps(C, KC_MAC, bytes, st, macs);
-    mac_kernel<<<(unsigned)blocks, thr, 0, st>>>(A);
+    if (C.q1()) mac_kernel<true><<<(unsigned)blocks, thr, 0, st>>>(A);
+    else mac_kernel<false><<<(unsigned)blocks, thr, 0, st>>>(A);
     return cudaGetLastError();
 }
 
 // Table launch of the key MAC: blockIdx.x = accumulator limb (product, x),
 // ordered by prime so that neighbouring blocks read the same key rows;
 // blockIdx.y = coefficient chunk.
+template <bool Q1>
 __global__ void __launch_bounds__(1024) mac_table_kernel(const MacJob *jobs, const MacTarget *targets, const u64 *keys,
                                                          i64 key_pstride, int key_digits, int alpha, int L, int N,
                                                          const ModQ *mods) {
@@ -465,7 +495,7 @@ __global__ void __launch_bounds__(1024) mac_table_kernel(const MacJob *jobs, con
     const bool isq = x < J.level;
     const int prime = isq ? x : L + (x - J.level);
     const i64 off = (i64)x * N + e;
-    mac_span<V>(J.d + off, J.dstride, J.ext + off, J.estride, J.n, J.nd, isq ? x / alpha : -1,
+    mac_span<V, Q1>(J.d + off, J.dstride, J.ext + off, J.estride, J.n, J.nd, isq ? x / alpha : -1,
                 keys + (i64)prime * N + e, key_pstride, key_digits, mods[prime], J.acc + off, J.astride);
 }
 
@@ -478,8 +508,12 @@ cudaError_t launch_mac_table(const Context &C, const MacJob *jobs, const MacTarg
     count_kernel(C);
     ProfScope ps(C, KC_MAC, bytes, st, macs);
     dim3 grid((unsigned)n_targets, (unsigned)chunks);
-    mac_table_kernel<<<grid, thr, 0, st>>>(jobs, targets, keys, (i64)(C.L + C.K) * C.N, C.dnum, C.alpha, C.L, C.N,
-                                           C.d_mods);
+    if (C.q1())
+        mac_table_kernel<true><<<grid, thr, 0, st>>>(jobs, targets, keys, (i64)(C.L + C.K) * C.N, C.dnum, C.alpha,
+                                                     C.L, C.N, C.d_mods);
+    else
+        mac_table_kernel<false><<<grid, thr, 0, st>>>(jobs, targets, keys, (i64)(C.L + C.K) * C.N, C.dnum, C.alpha,
+                                                      C.L, C.N, C.d_mods);
     return cudaGetLastError();
 }
 

@@ -65,6 +65,11 @@ def is_prime(n: int) -> bool:
 
 
 NTT_CONGRUENCE = 1 << 17  # q = 1 mod 2^17 serves every N <= 2^16
+# q = 1 mod 2^32 (q = h 2^32 + 1): still NTT-friendly for every N <= 2^31, and
+# the modular products of the GPU kernels take a cheaper form for it. The
+# named workloads below use such primes; make_params keeps 2^17 by default so
+# that the general forms stay exercised.
+Q1_CONGRUENCE = 1 << 32
 
 
 def prime_chain(bits: int, count: int, exclude=(), congruence: int = NTT_CONGRUENCE) -> list[int]:
@@ -109,34 +114,35 @@ class Params:
         return -(-self.L // self.dnum)
 
 
-def make_params(log_n: int, q_bits, k_special: int, dnum: int, p_bits: int = 60) -> Params:
+def make_params(log_n: int, q_bits, k_special: int, dnum: int, p_bits: int = 60,
+                congruence: int = NTT_CONGRUENCE) -> Params:
     """q_bits: list of bit sizes, one per Q prime (q_0 first). Primes of the same
     size are taken in descending order; special primes are the next primes of
-    p_bits bits not already used."""
+    p_bits bits not already used; every prime is 1 (mod congruence)."""
     used: list[int] = []
     q = []
     for b in q_bits:
-        nxt = prime_chain(b, 1, exclude=used)[0]
+        nxt = prime_chain(b, 1, exclude=used, congruence=congruence)[0]
         q.append(nxt)
         used.append(nxt)
-    p = prime_chain(p_bits, k_special, exclude=used)
+    p = prime_chain(p_bits, k_special, exclude=used, congruence=congruence)
     return Params(log_n, tuple(q), tuple(p), dnum)
 
 
 # The five workloads (sizes from the paper's 3-input and k-input settings).
-def params_small(log_n=10, dnum=1):
+def params_small(log_n=10, dnum=1, congruence=Q1_CONGRUENCE):
     """4 x 50-bit Q primes, one 60-bit special prime."""
-    return make_params(log_n, [50] * 4, 1, dnum)
+    return make_params(log_n, [50] * 4, 1, dnum, congruence=congruence)
 
 
-def params_mid(log_n=14):
+def params_mid(log_n=14, congruence=Q1_CONGRUENCE):
     """12 Q primes (q_0 60-bit, q_1..q_11 45-bit), 4 x 60-bit special, dnum 3."""
-    return make_params(log_n, [60] + [45] * 11, 4, 3)
+    return make_params(log_n, [60] + [45] * 11, 4, 3, congruence=congruence)
 
 
-def params_large(log_n=16, L=24, K=8, dnum=3):
+def params_large(log_n=16, L=24, K=8, dnum=3, congruence=Q1_CONGRUENCE):
     """24 x 50-bit Q primes, 8 x 60-bit special primes, dnum 3."""
-    return make_params(log_n, [50] * L, K, dnum)
+    return make_params(log_n, [50] * L, K, dnum, congruence=congruence)
 
 
 # ----------------------------------------------------------------------------

@@ -148,3 +148,25 @@ def test_precision_criterion_minimises_inner_degree():
         assert d <= inner_degree(P.TABLE_II[k], k)
     assert inner_degree(G.plan_optimize(12, "precision", 24, 8, 8)[0], 12) == 4
     assert inner_degree(G.plan_optimize(6, "precision", 24, 8, 8)[0], 6) == 2
+
+
+def test_workload_primes_and_peak_form_check(L):
+    """The named workloads use primes = 1 (mod 2^32), the form the kernels'
+    cheaper modular products need (q = h 2^32 + 1 stays NTT-friendly for
+    every N <= 2^31); make_params keeps the general form by default. The
+    integer-peak entry point rejects the cheaper-form kinds for any other
+    prime before it launches anything."""
+    import synth
+    for params in (synth.params_small(), synth.params_mid(), synth.params_large()):
+        for x in params.q + params.p:
+            assert x % synth.Q1_CONGRUENCE == 1 and synth.is_prime(x)
+            assert (x - 1) % (2 * params.N) == 0
+        assert len(set(params.q + params.p)) == params.L + params.K
+    general = synth.make_params(10, [50] * 4, 1, 1)
+    assert any(x % synth.Q1_CONGRUENCE != 1 for x in general.q + general.p)
+    chains = L.ckks_peak_chains()
+    w = (ctypes.c_uint64 * chains)(*([1] * chains))
+    q = general.q[0]
+    assert q % synth.Q1_CONGRUENCE != 1
+    for kind in (6, 7):
+        assert L.ckks_peak_int(kind, q, w, w, 1, 32, 1, ctypes.c_void_p(8), None) == -1

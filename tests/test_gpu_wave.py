@@ -159,11 +159,14 @@ def test_wave_rejects_one_phase_ring():
     assert e.value.code == -1
 
 
-@pytest.mark.parametrize("log_n", [14, 16])
-def test_wave_full_parameter_set(log_n):
+@pytest.mark.parametrize("log_n,congruence", [(14, synth.NTT_CONGRUENCE), (14, synth.Q1_CONGRUENCE),
+                                               (16, synth.Q1_CONGRUENCE)])
+def test_wave_full_parameter_set(log_n, congruence):
     """N = 2^14 / 2^16, L = 24, K = 8, dnum = 3: a mixed wave equals
-    ckks_mul_k alone on every product and the oracle on two sampled ones."""
-    S = Setup(synth.params_large(log_n), 12, 42)
+    ckks_mul_k alone on every product and the oracle on two sampled ones;
+    with primes = 1 (mod 2^17) (the general modular products) and = 1 (mod
+    2^32) (the cheaper forms)."""
+    S = Setup(synth.params_large(log_n, congruence=congruence), 12, 42)
     n = 16 if log_n == 14 else 7
     items = _mix(S, n, 10 + log_n, ks=[2, 3, 4, 5, 7, 8, 12], other_parts=False)
     _run_wave(S, items)
