@@ -312,10 +312,12 @@ def run_ours(args, rank, world, local_rank):
                             "frac": round(achieved_gbs / hbm_peak, 4),
                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"},
                     "fmaheavy_busy": busy,
-                    "limiter": "integer multiply (fmaheavy) pipe, not HBM: ncu shows it 64-73 % busy in the NTT "
-                               "phases (95 % in the register-only butterfly stream the peak comes from), 62-66 of its "
-                               "instructions per element for 4 butterflies, DRAM at 26 % of peak and traffic at most "
-                               "the algorithmic bytes (profiles/ntt_phase_N65536_batch8.md, int_peaks_gb300.md)"}
+                    "limiter": "integer multiply (fmaheavy) pipe and the latency around it, not HBM: ncu shows the "
+                               "pipe 63-72 % busy in the NTT phases (95 % in the register-only butterfly stream the "
+                               "peak comes from), 59-61 of its instructions per element for 4 butterflies, the rest "
+                               "of the issue slots lost to long-scoreboard and dependent-multiply stalls, DRAM at a "
+                               "quarter of peak and traffic at most the algorithmic bytes "
+                               "(profiles/ntt_phase_N65536_batch8.md, int_peaks_gb300.md)"}
     def int_frac(n, v):
         pk = int_peaks.get(op_unit(n))
         return round(v["int_ops"] / (v["total_ms"] / 1e3) / pk, 4) if pk and v["int_ops"] else None

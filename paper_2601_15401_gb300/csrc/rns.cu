@@ -122,8 +122,15 @@ __device__ __forceinline__ void tensor_coeff(const V &v, i64 r, int j, const Mod
         if (t < ncur) dst[(i64)t * ds] = mont_mul_t<Q1>(cur[t], fix, m);
 }
 
+// Three CTAs of 256 threads per SM (at most 85 registers) up to 9-term
+// tuples; two for the largest.
+template <int MAXT>
+struct TensorOcc {
+    static constexpr int minb = MAXT <= 9 ? 3 : 2;
+};
+
 template <int MAXT, bool Q1>
-__global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
+__global__ void __launch_bounds__(kThreads, TensorOcc<MAXT>::minb) tensor_kernel(TensorArgs A) {
     const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;  // limb * N + coefficient
     if (r >= (i64)A.level * A.N) return;
     const int j = (int)(r >> A.log_n);
@@ -133,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) tensor_kernel(TensorArgs A) {
 // Table launch: blockIdx.y = tree node; the node's entry is staged in shared
 // memory (it is indexed by child at run time).
 template <int MAXT, bool Q1>
-__global__ void __launch_bounds__(kThreads) tensor_table_kernel(const TensorJob *jobs, int N, int log_n,
+__global__ void __launch_bounds__(kThreads, TensorOcc<MAXT>::minb) tensor_table_kernel(const TensorJob *jobs, int N, int log_n,
                                                                 const ModQ *mods, const u64 *rpow) {
     __shared__ TensorJob J;
     {
