@@ -554,7 +554,8 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     import paper_2601_15401_gb300 as G
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    n_pull = B if args.h2d == "pull" else 0 if args.h2d == "copy" else int(round(B * args.pull_fraction))
+    n_mixed = int(round(B * args.pull_fraction))
+    npull = [B if args.h2d == "pull" else 0 if args.h2d == "copy" else n_mixed]
     # device buffer sets (inputs, outputs): one for the batched engine, two
     # alternating sets for the wave engine
     sets = [(dev_inp, dev_out)]
@@ -583,12 +584,14 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     def upload(k, b, cs):
         """One batch element's inputs host -> device on stream cs: by the copy
         engines (cudaMemcpyAsync) or by the GPU's own loads over the host link
-        (ckks_pull). "mixed" (default) sends the last pull_fraction of the
-        batch elements through the GPU's loads: the copy engines restart at a
+        (ckks_pull). "mixed" sends the last pull_fraction of the batch
+        elements through the GPU's loads: the copy engines restart at a
         fraction of the link's rate after device compute, and the GPU's loads
-        take SM slots from the multiplies, so each carries part."""
+        take SM slots from the multiplies, so each carries part; "pull" sends
+        every element through the GPU's loads; "auto" (default) keeps the
+        faster of the two."""
         dst = sets[cur_set[0]][0][k][b]
-        if b >= B - n_pull:
+        if b >= B - npull[0]:
             G.pull(dst, host_in[b, :k], blocks=sms * args.pull_ctas_per_sm, stream=cs)
         else:
             dst.copy_(host_in[b, :k], non_blocking=True)
@@ -688,6 +691,26 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize()
+    trials = {}
+    if args.h2d == "auto":
+        # the copy engines' rate next to device compute differs between
+        # boxes (94-210 GB/s measured), the GPU's own loads hold ~210 GB/s
+        # but take SM slots: time two untimed steps of each split and keep
+        # the faster
+        for n in sorted({n_mixed, B}):
+            npull[0] = n
+            step()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(2):
+                step()
+            if last_fin[0] is not None:
+                stream.wait_event(last_fin[0])
+            t1.record(stream)
+            t1.synchronize()
+            trials[n] = t0.elapsed_time(t1) / 2
+        npull[0] = min(trials, key=trials.get)
+        torch.cuda.synchronize()
     cur_set[0] = 0
     bw_before = upload_alone()
     steps = max(1, args.steps)
@@ -710,8 +733,10 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
             "h2d_GBps_alone": [round(bw_before, 1), round(bw_after, 1)],
             "h2d_GBps_warmup": [round(x, 1) for x in warm_bw],
             "copy_streams": len(copies), "host_numa": numa_note,
-            "h2d": {"copy_engines_elements": B - n_pull, "gpu_load_elements": n_pull,
-                    "gpu_load_ctas": sms * args.pull_ctas_per_sm if n_pull else 0,
+            "h2d": {"copy_engines_elements": B - npull[0], "gpu_load_elements": npull[0],
+                    "gpu_load_ctas": sms * args.pull_ctas_per_sm if npull[0] else 0,
+                    "split": args.h2d,
+                    "trial_ms_per_step": {f"{B - n} copy / {n} gpu-load": round(v, 2) for n, v in trials.items()},
                     "note": "per step, of the B batch elements of every k: copy engines (cudaMemcpyAsync) for the "
                             "first, the GPU's own loads over the host link (ckks_pull, 64-thread CTAs) for the rest"},
             "engine": "one cross-shape wave per step, two alternating input / output sets" if waves_mode else
@@ -807,10 +832,11 @@ def main():
     ap.add_argument("--ks", default="")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--h2d", default="mixed", choices=["mixed", "pull", "copy"],
-                    help="e2e uploads: copy engines, GPU loads over the host link (pull), or both (mixed)")
+    ap.add_argument("--h2d", default="auto", choices=["auto", "mixed", "pull", "copy"],
+                    help="e2e uploads: copy engines, GPU loads over the host link (pull), both (mixed), or the "
+                         "faster of mixed and pull in two untimed steps each (auto)")
     ap.add_argument("--pull-fraction", type=float, default=0.25,
-                    help="--h2d mixed: share of the batch elements uploaded by GPU loads")
+                    help="--h2d mixed / auto: share of the batch elements uploaded by GPU loads")
     ap.add_argument("--pull-ctas-per-sm", type=int, default=1, help="64-thread CTAs per SM of the e2e uploads")
     ap.add_argument("--copy-streams", type=int, default=1,
                     help="streams the e2e leg spreads its copies over (1 measured best: 465 vs 343 with 4)")

@@ -111,9 +111,11 @@ int ckks_keygen_evk(ckks_context *ctx, uint32_t t_max, const int64_t *s, const u
                     uint64_t *keys, void *workspace, size_t ws_bytes, void *stream);
 
 /* ckks_evk_set_create: adopts a key buffer in the layout above for
- * t = 2..t_max. The buffer is converted IN PLACE to the library's internal
- * form (Montgomery form; P^-1 folded into the Q rows, Eq. 12) and is
- * borrowed until ckks_evk_set_destroy; do not read it as plain keys after. */
+ * t = 2..t_max; the buffer must be 16-byte aligned (CKKS_EINVAL otherwise:
+ * the key MAC reads it with 16-byte loads). The buffer is converted IN
+ * PLACE to the library's internal form (Montgomery form; P^-1 folded into
+ * the Q rows, Eq. 12) and is borrowed until ckks_evk_set_destroy; do not
+ * read it as plain keys after. */
 int ckks_evk_set_create(ckks_context *ctx, uint32_t t_max, uint64_t *keys, void *stream, ckks_evk_set **out);
 void ckks_evk_set_destroy(ckks_evk_set *set);
 

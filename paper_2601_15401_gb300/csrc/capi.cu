@@ -144,8 +144,10 @@ int ckks_keygen_evk(ckks_context *ctx, uint32_t t_max, const int64_t *s, const u
 }
 
 int ckks_evk_set_create(ckks_context *ctx, uint32_t t_max, uint64_t *keys, void *stream, ckks_evk_set **out) {
-    if (!ctx || !keys || !out || t_max < 2 || t_max > 13) return CKKS_EINVAL;
+    if (!out) return CKKS_EINVAL;
     *out = nullptr;
+    // the key MAC reads keys with 16-byte loads
+    if (!ctx || !keys || t_max < 2 || t_max > 13 || (uintptr_t)keys % 16) return CKKS_EINVAL;
     const Context &C = ctx->c;
     cudaSetDevice(C.device);
     long long rows = (long long)(t_max - 1) * C.dnum * 2 * (C.L + C.K);

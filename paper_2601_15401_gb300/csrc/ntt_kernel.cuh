@@ -464,6 +464,9 @@ struct PhaseLaunch {
 #ifndef CKKS_NTT_FAST_MINB
 #define CKKS_NTT_FAST_MINB 3    // fixed modes: 80 registers, three CTAs per SM
 #endif
+#ifndef CKKS_NTT_COLS_MINB
+#define CKKS_NTT_COLS_MINB CKKS_NTT_FAST_MINB   // fixed-mode column phases
+#endif
 #ifndef CKKS_NTT_EQ17_MINB
 #define CKKS_NTT_EQ17_MINB 3    // the Eq. 17 load spills a little at 80 registers; three CTAs per SM
                                 // still run the phase 9 % faster than two at 128
@@ -521,7 +524,7 @@ static inline cudaError_t dispatch_fast(bool cols, int logn, const NttPhase &P, 
     if (logn == LG) {                                                                              \
         if constexpr (FWD) {                                                                       \
             if (cols && S.mode == ST_LAZY) {                                                       \
-                if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB, Q1); \
+                if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_LAZY, CKKS_NTT_COLS_MINB, Q1); \
                 if (L.mode == LD_EQ17) CKKS_LAUNCH(LG, true, LD_EQ17, ST_LAZY, CKKS_NTT_EQ17_MINB, Q1);   \
             }                                                                                      \
             if (!cols && L.mode == LD_PLAIN) {                                                     \
@@ -534,8 +537,8 @@ static inline cudaError_t dispatch_fast(bool cols, int logn, const NttPhase &P, 
                 if (L.mode == LD_ADD) CKKS_LAUNCH(LG, false, LD_ADD, ST_LAZY, CKKS_NTT_FAST_MINB, Q1);    \
             }                                                                                      \
             if (cols && L.mode == LD_PLAIN) {                                                      \
-                if (S.mode == ST_SCALE) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_SCALE, CKKS_NTT_FAST_MINB, Q1); \
-                if (S.mode == ST_MODDOWN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_MODDOWN, CKKS_NTT_FAST_MINB, Q1); \
+                if (S.mode == ST_SCALE) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_SCALE, CKKS_NTT_COLS_MINB, Q1); \
+                if (S.mode == ST_MODDOWN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_MODDOWN, CKKS_NTT_COLS_MINB, Q1); \
             }                                                                                      \
         }                                                                                          \
     }

@@ -19,6 +19,33 @@ namespace ckks {
 
 static constexpr int kThreads = 256;
 
+// V adjacent words at p (16-byte loads / stores for even V; p 16-byte aligned)
+template <int V>
+__device__ __forceinline__ void load_span(const u64 *p, u64 (&o)[V]) {
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p + i);
+            o[i] = v.x;
+            o[i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) o[i] = p[i];
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void store_span(u64 *p, const u64 (&v)[V]) {
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2) *reinterpret_cast<ulonglong2 *>(p + i) = make_ulonglong2(v[i], v[i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) p[i] = v[i];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // tensor product: out = prod over children of (sum_l c_l s^l), coefficient-
 // wise in the NTT domain. Each child product is a Montgomery product, so the
@@ -49,77 +76,101 @@ struct TensorTableView {
 
 // MAXT bounds every tuple size involved (children and output), so the
 // unrolled, predicated product loops stay short for small nodes.
-// r = limb * N + coefficient, j = the limb's prime.
-template <int MAXT, bool Q1, class V>
-__device__ __forceinline__ void tensor_coeff(const V &v, i64 r, int j, const ModQ m, const u64 *rpow) {
+// r = limb * N + coefficient (the first of V adjacent ones), j = the limb's
+// prime.
+template <int MAXT, bool Q1, int V, class View>
+__device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const ModQ m, const u64 *rpow) {
     const u64 q = m.q;
-    u64 cur[MAXT];
+    u64 cur[MAXT][V];
     int ncur = v.polys(0);
     {
         const u64 *src = v.src(0) + r;
         const i64 ps = v.pstride(0);
 #pragma unroll
-        for (int a = 0; a < MAXT; ++a) cur[a] = a < ncur ? src[(i64)a * ps] : 0ull;
+        for (int a = 0; a < MAXT; ++a) {
+            if (a < ncur) load_span<V>(src + (i64)a * ps, cur[a]);
+            else
+#pragma unroll
+                for (int e = 0; e < V; ++e) cur[a][e] = 0ull;
+        }
     }
     for (int c = 1; c < v.m(); ++c) {
         const int ny = v.polys(c);
         const u64 *src = v.src(c) + r;
         const i64 ps = v.pstride(c);
-        u64 y[MAXT];
+        u64 y[MAXT][V];
 #pragma unroll
-        for (int a = 0; a < MAXT; ++a) y[a] = a < ny ? src[(i64)a * ps] : 0ull;
-        u64 nxt[MAXT];
-        if (ny == 2) {
-            // times a ciphertext (y0 + y1 s): Karatsuba on pairs of the running
-            // tuple (Fig. 2(b)): for (c_a, c_{a+1}) the cross term
-            // c_a y1 + c_{a+1} y0 = (c_a + c_{a+1})(y0 + y1) - c_a y0 - c_{a+1} y1,
-            // an exact non-negative integer, so it stays in the 128-bit sums.
-            Acc128 acc[MAXT];
+        for (int a = 0; a < MAXT; ++a) {
+            if (a < ny) load_span<V>(src + (i64)a * ps, y[a]);
+            else
 #pragma unroll
-            for (int t = 0; t < MAXT; ++t) acc[t].zero();
-            const u64 ys = y[0] + y[1];  // < 2q, not reduced
+                for (int e = 0; e < V; ++e) y[a][e] = 0ull;
+        }
+        u64 nxt[MAXT][V];
 #pragma unroll
-            for (int a = 0; a < MAXT; a += 2) {
-                if (a + 1 < ncur && a + 2 < MAXT) {
-                    const u64 p1h = mulhi64(cur[a], y[0]), p1l = cur[a] * y[0];
-                    const u64 p2h = mulhi64(cur[a + 1], y[1]), p2l = cur[a + 1] * y[1];
-                    const u64 s = cur[a] + cur[a + 1];
-                    u64 p3l = s * ys, p3h = mulhi64(s, ys);
-                    // p3 -= p1 + p2 (128-bit; the result is c_a y1 + c_{a+1} y0 >= 0)
-                    u64 bl = p1l + p2l, bh = p1h + p2h + (bl < p1l ? 1ull : 0ull);
-                    u64 rl = p3l - bl, rh = p3h - bh - (p3l < bl ? 1ull : 0ull);
-                    acc[a].add(p1h, p1l, q);
-                    acc[a + 1].add(rh, rl, q);
-                    acc[a + 2].add(p2h, p2l, q);
-                } else if (a < ncur && a + 1 >= ncur) {
-                    acc[a].mac(cur[a], y[0], q);
-                    if (a + 1 < MAXT) acc[a + 1].mac(cur[a], y[1], q);
+        for (int e = 0; e < V; ++e) {
+            if (ny == 2) {
+                // times a ciphertext (y0 + y1 s): Karatsuba on pairs of the running
+                // tuple (Fig. 2(b)): for (c_a, c_{a+1}) the cross term
+                // c_a y1 + c_{a+1} y0 = (c_a + c_{a+1})(y0 + y1) - c_a y0 - c_{a+1} y1,
+                // an exact non-negative integer, so it stays in the 128-bit sums.
+                Acc128 acc[MAXT];
+#pragma unroll
+                for (int t = 0; t < MAXT; ++t) acc[t].zero();
+                const u64 y0 = y[0][e], y1 = y[1][e];
+                const u64 ys = y0 + y1;  // < 2q, not reduced
+#pragma unroll
+                for (int a = 0; a < MAXT; a += 2) {
+                    if (a + 1 < ncur && a + 2 < MAXT) {
+                        const u64 ca = cur[a][e], cb = cur[a + 1][e];
+                        const u64 p1h = mulhi64(ca, y0), p1l = ca * y0;
+                        const u64 p2h = mulhi64(cb, y1), p2l = cb * y1;
+                        const u64 sab = ca + cb;
+                        u64 p3l = sab * ys, p3h = mulhi64(sab, ys);
+                        // p3 -= p1 + p2 (128-bit; the result is c_a y1 + c_{a+1} y0 >= 0)
+                        u64 bl = p1l + p2l, bh = p1h + p2h + (bl < p1l ? 1ull : 0ull);
+                        u64 rl = p3l - bl, rh = p3h - bh - (p3l < bl ? 1ull : 0ull);
+                        acc[a].add(p1h, p1l, q);
+                        acc[a + 1].add(rh, rl, q);
+                        acc[a + 2].add(p2h, p2l, q);
+                    } else if (a < ncur && a + 1 >= ncur) {
+                        acc[a].mac(cur[a][e], y0, q);
+                        if (a + 1 < MAXT) acc[a + 1].mac(cur[a][e], y1, q);
+                    }
                 }
-            }
 #pragma unroll
-            for (int t = 0; t < MAXT; ++t) nxt[t] = t < ncur + 1 ? redc_t<Q1>(acc[t].hi, acc[t].lo, m) : 0ull;
-        } else {
+                for (int t = 0; t < MAXT; ++t)
+                    nxt[t][e] = t < ncur + 1 ? redc_t<Q1>(acc[t].hi, acc[t].lo, m) : 0ull;
+            } else {
 #pragma unroll
-            for (int t = 0; t < MAXT; ++t) {
-                Acc128 acc;
-                acc.zero();
+                for (int t = 0; t < MAXT; ++t) {
+                    Acc128 acc;
+                    acc.zero();
 #pragma unroll
-                for (int a = 0; a <= t; ++a) {
-                    if (a < ncur && t - a < ny) acc.mac(cur[a], y[t - a], q);
+                    for (int a = 0; a <= t; ++a) {
+                        if (a < ncur && t - a < ny) acc.mac(cur[a][e], y[t - a][e], q);
+                    }
+                    nxt[t][e] = t < ncur + ny - 1 ? redc_t<Q1>(acc.hi, acc.lo, m) : 0ull;
                 }
-                nxt[t] = t < ncur + ny - 1 ? redc_t<Q1>(acc.hi, acc.lo, m) : 0ull;
             }
         }
         ncur = ncur + ny - 1;
 #pragma unroll
-        for (int t = 0; t < MAXT; ++t) cur[t] = nxt[t];
+        for (int t = 0; t < MAXT; ++t)
+#pragma unroll
+            for (int e = 0; e < V; ++e) cur[t][e] = nxt[t][e];
     }
     const u64 fix = rpow[(i64)j * 16 + v.m()];  // R^m
     u64 *dst = v.dst() + r;
     const i64 ds = v.dstride();
 #pragma unroll
     for (int t = 0; t < MAXT; ++t)
-        if (t < ncur) dst[(i64)t * ds] = mont_mul_t<Q1>(cur[t], fix, m);
+        if (t < ncur) {
+            u64 o[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) o[e] = mont_mul_t<Q1>(cur[t][e], fix, m);
+            store_span<V>(dst + (i64)t * ds, o);
+        }
 }
 
 // Three CTAs of 256 threads per SM (at most 85 registers) up to 9-term
@@ -129,17 +180,17 @@ struct TensorOcc {
     static constexpr int minb = MAXT <= 9 ? 3 : 2;
 };
 
-template <int MAXT, bool Q1>
+template <int MAXT, bool Q1, int V>
 __global__ void __launch_bounds__(kThreads, TensorOcc<MAXT>::minb) tensor_kernel(TensorArgs A) {
-    const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;  // limb * N + coefficient
+    const i64 r = ((i64)blockIdx.x * blockDim.x + threadIdx.x) * V;  // limb * N + coefficient
     if (r >= (i64)A.level * A.N) return;
     const int j = (int)(r >> A.log_n);
-    tensor_coeff<MAXT, Q1>(TensorUniformView{A, (int)blockIdx.y}, r, j, A.mods[j], A.rpow);
+    tensor_coeff<MAXT, Q1, V>(TensorUniformView{A, (int)blockIdx.y}, r, j, A.mods[j], A.rpow);
 }
 
 // Table launch: blockIdx.y = tree node; the node's entry is staged in shared
 // memory (it is indexed by child at run time).
-template <int MAXT, bool Q1>
+template <int MAXT, bool Q1, int V>
 __global__ void __launch_bounds__(kThreads, TensorOcc<MAXT>::minb) tensor_table_kernel(const TensorJob *jobs, int N, int log_n,
                                                                 const ModQ *mods, const u64 *rpow) {
     __shared__ TensorJob J;
@@ -152,10 +203,10 @@ __global__ void __launch_bounds__(kThreads, TensorOcc<MAXT>::minb) tensor_table_
         for (int i = threadIdx.x; i < W; i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const i64 r = ((i64)blockIdx.x * blockDim.x + threadIdx.x) * V;
     if (r >= (i64)J.level * N) return;
     const int j = (int)(r >> log_n);
-    tensor_coeff<MAXT, Q1>(TensorTableView{J}, r, j, mods[j], rpow);
+    tensor_coeff<MAXT, Q1, V>(TensorTableView{J}, r, j, mods[j], rpow);
 }
 
 // 64 x 64 -> 128-bit products per coefficient of a node's tensor product
@@ -174,56 +225,93 @@ double tensor_products_per_coeff(const int *polys, int m) {
     return ops + ncur;  // the final R^m correction
 }
 
-template <bool Q1>
+// Tuples of up to 4 terms take two adjacent coefficients per thread
+// (16-byte loads and stores) when every pointer is 16-byte aligned and every
+// stride even; larger tuples (more live terms per coefficient) one.
+constexpr int kTensorVecMaxT = 4;
+
+template <bool Q1, int V>
 static void launch_tensor_sized(int maxt, dim3 blocks, const TensorArgs &A, cudaStream_t st) {
-    if (maxt <= 3) tensor_kernel<3, Q1><<<blocks, kThreads, 0, st>>>(A);
-    else if (maxt <= 4) tensor_kernel<4, Q1><<<blocks, kThreads, 0, st>>>(A);
-    else if (maxt <= 5) tensor_kernel<5, Q1><<<blocks, kThreads, 0, st>>>(A);
-    else if (maxt <= 7) tensor_kernel<7, Q1><<<blocks, kThreads, 0, st>>>(A);
-    else if (maxt <= 9) tensor_kernel<9, Q1><<<blocks, kThreads, 0, st>>>(A);
-    else tensor_kernel<CKKS_MAX_TUPLE, Q1><<<blocks, kThreads, 0, st>>>(A);
+    if (maxt <= 3) tensor_kernel<3, Q1, V><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 4) tensor_kernel<4, Q1, V><<<blocks, kThreads, 0, st>>>(A);
+    else if constexpr (V == 1) {
+        if (maxt <= 5) tensor_kernel<5, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
+        else if (maxt <= 7) tensor_kernel<7, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
+        else if (maxt <= 9) tensor_kernel<9, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
+        else tensor_kernel<CKKS_MAX_TUPLE, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
+    }
 }
 
-template <bool Q1>
+template <bool Q1, int V>
 static void launch_tensor_table_sized(const Context &C, int maxt, dim3 blocks, const TensorJob *jobs,
                                       cudaStream_t st) {
-    if (maxt <= 3) tensor_table_kernel<3, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else if (maxt <= 4) tensor_table_kernel<4, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else if (maxt <= 5) tensor_table_kernel<5, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else if (maxt <= 7) tensor_table_kernel<7, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else if (maxt <= 9) tensor_table_kernel<9, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
-    else tensor_table_kernel<CKKS_MAX_TUPLE, Q1><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow);
+#define CKKS_TT(MT, VV) tensor_table_kernel<MT, Q1, VV><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow)
+    if (maxt <= 3) CKKS_TT(3, V);
+    else if (maxt <= 4) CKKS_TT(4, V);
+    else if constexpr (V == 1) {
+        if (maxt <= 5) CKKS_TT(5, 1);
+        else if (maxt <= 7) CKKS_TT(7, 1);
+        else if (maxt <= 9) CKKS_TT(9, 1);
+        else CKKS_TT(CKKS_MAX_TUPLE, 1);
+    }
+#undef CKKS_TT
+}
+
+static bool view_vec2(const LimbView &v) {
+    return ((uintptr_t)v.ptr % 16) == 0 && v.bstride % 2 == 0 && v.pstride % 2 == 0;
 }
 
 cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t st) {
     TensorArgs A = Ain;
     A.log_n = C.log_n;
-    dim3 blocks((unsigned)(((i64)A.level * A.N + kThreads - 1) / kThreads), A.n_batch);
     count_kernel(C);
     int in_polys = 0, maxt = 0;
+    bool vec2 = view_vec2(A.out);
     for (int c = 0; c < A.m; ++c) {
         in_polys += A.child_polys[c];
         maxt = std::max(maxt, A.child_polys[c]);
+        vec2 = vec2 && view_vec2(A.child[c]);
     }
     int out_polys = in_polys - A.m + 1;
     maxt = std::max(maxt, out_polys);
+    vec2 = vec2 && maxt <= kTensorVecMaxT;
     const double coeffs = (double)A.n_batch * A.level * A.N;
     ProfScope ps(C, KC_TENSOR, (double)(in_polys + out_polys) * coeffs * sizeof(u64), st,
                  coeffs * tensor_products_per_coeff(A.child_polys, A.m));
-    if (C.q1()) launch_tensor_sized<true>(maxt, blocks, A, st);
-    else launch_tensor_sized<false>(maxt, blocks, A, st);
+    const i64 per = vec2 ? 2 * kThreads : kThreads;
+    dim3 blocks((unsigned)(((i64)A.level * A.N + per - 1) / per), A.n_batch);
+    if (vec2) {
+        if (C.q1()) launch_tensor_sized<true, 2>(maxt, blocks, A, st);
+        else launch_tensor_sized<false, 2>(maxt, blocks, A, st);
+    } else {
+        if (C.q1()) launch_tensor_sized<true, 1>(maxt, blocks, A, st);
+        else launch_tensor_sized<false, 1>(maxt, blocks, A, st);
+    }
     return cudaGetLastError();
 }
 
+bool tensor_job_vec2(const TensorJob &T) {
+    bool ok = ((uintptr_t)T.out % 16) == 0 && T.ostride % 2 == 0;
+    for (int c = 0; c < T.m; ++c) ok = ok && ((uintptr_t)T.child[c] % 16) == 0 && T.cstride[c] % 2 == 0;
+    return ok;
+}
+
 cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_jobs, int maxt, int max_level,
-                                double bytes, double ops, cudaStream_t st) {
+                                bool vec2, double bytes, double ops, cudaStream_t st) {
     if (n_jobs <= 0) return cudaSuccess;
     if (n_jobs > 65535) return cudaErrorInvalidValue;
-    dim3 blocks((unsigned)(((i64)max_level * C.N + kThreads - 1) / kThreads), (unsigned)n_jobs);
+    vec2 = vec2 && maxt <= kTensorVecMaxT;
+    const i64 per = vec2 ? 2 * kThreads : kThreads;
+    dim3 blocks((unsigned)(((i64)max_level * C.N + per - 1) / per), (unsigned)n_jobs);
     count_kernel(C);
     ProfScope ps(C, KC_TENSOR, bytes, st, ops);
-    if (C.q1()) launch_tensor_table_sized<true>(C, maxt, blocks, jobs, st);
-    else launch_tensor_table_sized<false>(C, maxt, blocks, jobs, st);
+    if (vec2) {
+        if (C.q1()) launch_tensor_table_sized<true, 2>(C, maxt, blocks, jobs, st);
+        else launch_tensor_table_sized<false, 2>(C, maxt, blocks, jobs, st);
+    } else {
+        if (C.q1()) launch_tensor_table_sized<true, 1>(C, maxt, blocks, jobs, st);
+        else launch_tensor_table_sized<false, 1>(C, maxt, blocks, jobs, st);
+    }
     return cudaGetLastError();
 }
 
@@ -233,34 +321,13 @@ cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_j
 // y'_j = [y_j (Q_beta/q_j)^-1]_{q_j} was produced by the INTT's epilogue.
 // blockIdx.y = (t, beta) job, blockIdx.z = batch.
 // ---------------------------------------------------------------------------
-// Coefficients per thread of the key MAC: two adjacent coefficients read
-// with 16-byte loads (twice the bytes in flight per load instruction; the
-// kernel is bound by load latency, not by its multiplies).
+// Coefficients per thread of the key MAC: four adjacent coefficients read
+// with two 16-byte loads per stream (more bytes in flight per thread; the
+// kernel is bound by load latency, not by its multiplies). Measured on the
+// bench step: 17.5 ms at four, 18.1 at two, 19.4 at one.
 #ifndef CKKS_MAC_VEC
-#define CKKS_MAC_VEC 2
+#define CKKS_MAC_VEC 4
 #endif
-
-template <int V>
-__device__ __forceinline__ void load_span(const u64 *p, u64 (&o)[V]) {
-    if constexpr (V == 2) {
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
-        o[0] = v.x;
-        o[1] = v.y;
-    } else {
-#pragma unroll
-        for (int i = 0; i < V; ++i) o[i] = p[i];
-    }
-}
-
-template <int V>
-__device__ __forceinline__ void store_span(u64 *p, const u64 (&v)[V]) {
-    if constexpr (V == 2) {
-        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(v[0], v[1]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < V; ++i) p[i] = v[i];
-    }
-}
 
 // Coefficients per thread of BConv (1: measured fastest; 2 was 3 % slower)
 #ifndef CKKS_BCONV_VEC

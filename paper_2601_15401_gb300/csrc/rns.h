@@ -89,8 +89,12 @@ struct MacTarget {                       // one accumulator limb x of product `j
 };
 
 cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st);
+// vec2: every entry's pointers are 16-byte aligned and its strides even
+// (tensor_job_vec2), so tuples of up to 4 terms may take two coefficients
+// per thread
+bool tensor_job_vec2(const TensorJob &T);
 cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_jobs, int maxt, int max_level,
-                                double bytes, double ops, cudaStream_t st);
+                                bool vec2, double bytes, double ops, cudaStream_t st);
 double tensor_products_per_coeff(const int *polys, int m);
 cudaError_t launch_rschain_table(const Context &C, const RsJob *jobs, int n_jobs, int max_polys, double bytes,
                                  cudaStream_t st);

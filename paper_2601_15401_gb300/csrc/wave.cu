@@ -59,6 +59,7 @@ struct Stage {
     LoadSpec L{};
     StoreSpec S{};
     int maxt = 0, max_level = 0, max_polys = 0;
+    bool vec2 = true;  // tensor: every entry 16-byte aligned with even strides
     std::vector<NttJob> ntt;
     std::vector<TensorJob> tensor;
     std::vector<RsJob> rs;
@@ -217,6 +218,7 @@ void build_product(Builder &B, const WaveProduct &w, Bump &ws) {
         if (emit) {
             Stage &s = B.at(round, cls, SK_TENSOR);
             s.tensor.push_back(T);
+            s.vec2 = s.vec2 && tensor_job_vec2(T);
             s.maxt = std::max(s.maxt, maxt);
             s.max_level = std::max(s.max_level, lv);
             s.bytes += (double)(in_polys + np) * lv * limb;
@@ -474,7 +476,8 @@ cudaError_t enqueue(ckks_wave &W, char *ws /* the job tables */, cudaStream_t st
                                        st);
             break;
         case SK_TENSOR:
-            e = launch_tensor_table(C, (const TensorJob *)(ws + s.off), n, s.maxt, s.max_level, s.bytes, s.ops, st);
+            e = launch_tensor_table(C, (const TensorJob *)(ws + s.off), n, s.maxt, s.max_level, s.vec2, s.bytes, s.ops,
+                                    st);
             break;
         case SK_RSCHAIN:
             e = launch_rschain_table(C, (const RsJob *)(ws + s.off), n, s.max_polys, s.bytes, st);

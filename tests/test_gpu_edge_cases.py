@@ -110,3 +110,53 @@ def test_workspace_and_size_queries_reject_bad_levels(env):
         with pytest.raises(G.CkksError) as e:
             call()
         assert e.value.code == ELEVEL
+
+
+@pytest.mark.parametrize("log_n", [6, 14])
+def test_inputs_at_odd_word_offsets(log_n):
+    """Tuples that start 8 bytes past a 16-byte boundary (or have odd
+    polynomial strides) are valid: the tensor kernels then read one
+    coefficient per thread instead of two (16-byte loads need 16-byte
+    alignment); the result equals the oracle's, in a single product and (N >
+    256) in a cross-shape wave."""
+    import paper_2601_15401_gb300 as G
+    from gpu_common import Setup, oracle_tuple
+    params = synth.make_params(log_n, [50] * 5, 2, 2, congruence=synth.Q1_CONGRUENCE)
+    S = Setup(params, 3, 303)
+    N, k, level = params.N, 3, 5
+    arrs = [synth.uniform_tuple(params, 2, level, 304, u) for u in range(k)]
+    want = O.mul_k(S.octx, [oracle_tuple(a) for a in arrs], S.okeys).data
+    depth = S.ctx.plan_describe(k)["depth"]
+    # one spare word in front of every tuple, so each starts at an odd word
+    flat = [torch.zeros(1 + 2 * level * N, dtype=torch.uint64, device="cuda") for _ in range(k)]
+    for f, a in zip(flat, arrs):
+        f[1:].copy_(dev(a).reshape(-1))
+    cts = [G.Tuple(f[1:].view(2, level, N), 2, level, level) for f in flat]
+    assert all(c.data.data_ptr() % 16 == 8 for c in cts)
+    out = G.Tuple.wrap(torch.zeros((2, level - depth, N), dtype=torch.uint64, device="cuda"))
+    ws = S.ws(S.ctx.workspace_size(k, level, 1))
+    S.ctx.mul_k(cts, S.evk, out, ws)
+    S.ctx.check()
+    assert np.array_equal(host(out.data), want)
+    if N <= 256:
+        return  # waves need the two-phase NTT (N > 256)
+    out2 = G.Tuple.wrap(torch.zeros_like(out.data))
+    w = G.Wave(S.ctx, [(cts, out2, None)], S.evk)
+    w.run(*w.buffers())
+    S.ctx.check()
+    assert np.array_equal(host(out2.data), want)
+
+
+def test_evk_set_rejects_unaligned_keys(env):
+    """The key MAC reads the evaluation keys with 16-byte loads, so a key
+    buffer that is not 16-byte aligned is refused before any launch."""
+    G, params, ctx, octx, okeys, evk = env
+    from paper_2601_15401_gb300._lib import lib
+    plain = np.stack([np.stack([np.stack([k[0], k[1]]) for k in row]) for row in okeys])
+    flat = torch.zeros(1 + plain.size, dtype=torch.uint64, device="cuda")
+    flat[1:].copy_(dev(plain).reshape(-1))
+    h = ctypes.c_void_p()
+    assert flat[1:].data_ptr() % 16 == 8
+    assert lib().ckks_evk_set_create(ctx._h, 4, ctypes.c_void_p(flat[1:].data_ptr()), None, ctypes.byref(h)) == EINVAL
+    assert not h.value
+    ctx.check()
