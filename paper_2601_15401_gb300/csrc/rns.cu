@@ -225,18 +225,21 @@ double tensor_products_per_coeff(const int *polys, int m) {
     return ops + ncur;  // the final R^m correction
 }
 
-// Tuples of up to 4 terms take two adjacent coefficients per thread
+// Tuples of up to 5 terms take two adjacent coefficients per thread
 // (16-byte loads and stores) when every pointer is 16-byte aligned and every
 // stride even; larger tuples (more live terms per coefficient) one.
-constexpr int kTensorVecMaxT = 4;
+#ifndef CKKS_TENSOR_VEC_MAXT
+#define CKKS_TENSOR_VEC_MAXT 5
+#endif
+constexpr int kTensorVecMaxT = CKKS_TENSOR_VEC_MAXT;
 
 template <bool Q1, int V>
 static void launch_tensor_sized(int maxt, dim3 blocks, const TensorArgs &A, cudaStream_t st) {
     if (maxt <= 3) tensor_kernel<3, Q1, V><<<blocks, kThreads, 0, st>>>(A);
     else if (maxt <= 4) tensor_kernel<4, Q1, V><<<blocks, kThreads, 0, st>>>(A);
+    else if (maxt <= 5 && (V == 1 || kTensorVecMaxT >= 5)) tensor_kernel<5, Q1, V><<<blocks, kThreads, 0, st>>>(A);
     else if constexpr (V == 1) {
-        if (maxt <= 5) tensor_kernel<5, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
-        else if (maxt <= 7) tensor_kernel<7, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
+        if (maxt <= 7) tensor_kernel<7, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
         else if (maxt <= 9) tensor_kernel<9, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
         else tensor_kernel<CKKS_MAX_TUPLE, Q1, 1><<<blocks, kThreads, 0, st>>>(A);
     }
@@ -248,9 +251,9 @@ static void launch_tensor_table_sized(const Context &C, int maxt, dim3 blocks, c
 #define CKKS_TT(MT, VV) tensor_table_kernel<MT, Q1, VV><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow)
     if (maxt <= 3) CKKS_TT(3, V);
     else if (maxt <= 4) CKKS_TT(4, V);
+    else if (maxt <= 5 && (V == 1 || kTensorVecMaxT >= 5)) CKKS_TT(5, V);
     else if constexpr (V == 1) {
-        if (maxt <= 5) CKKS_TT(5, 1);
-        else if (maxt <= 7) CKKS_TT(7, 1);
+        if (maxt <= 7) CKKS_TT(7, 1);
         else if (maxt <= 9) CKKS_TT(9, 1);
         else CKKS_TT(CKKS_MAX_TUPLE, 1);
     }
@@ -328,6 +331,12 @@ cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_j
 #ifndef CKKS_MAC_VEC
 #define CKKS_MAC_VEC 4
 #endif
+// Largest key-MAC block (the "mac_threads" tunable's upper bound). At 1024
+// the four-coefficient form gets 64 registers and spills 96-196 bytes a
+// thread to L1; bounding the block at 512 removed the spills (106
+// registers) but cut the resident warps, and the MAC took 20.3 instead of
+// 17.5 ms per bench step.
+#define CKKS_MAC_MAX_THREADS 1024
 
 // Coefficients per thread of BConv (1: measured fastest; 2 was 3 % slower)
 #ifndef CKKS_BCONV_VEC
@@ -516,7 +525,7 @@ __device__ __forceinline__ void mac_span(const u64 *dsrc, i64 dstride, const u64
 }
 
 template <bool Q1>
-__global__ void __launch_bounds__(1024) mac_kernel(MacArgs A) {
+__global__ void __launch_bounds__(CKKS_MAC_MAX_THREADS) mac_kernel(MacArgs A) {
     constexpr int V = CKKS_MAC_VEC;
     const int chunks = (A.N + blockDim.x * V - 1) / (blockDim.x * V);
     // block order: batch fastest, then chunk, then limb -> blocks that share a
@@ -557,7 +566,7 @@ cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
 // ordered by prime so that neighbouring blocks read the same key rows;
 // blockIdx.y = coefficient chunk.
 template <bool Q1>
-__global__ void __launch_bounds__(1024) mac_table_kernel(const MacJob *jobs, const MacTarget *targets, const u64 *keys,
+__global__ void __launch_bounds__(CKKS_MAC_MAX_THREADS) mac_table_kernel(const MacJob *jobs, const MacTarget *targets, const u64 *keys,
                                                          i64 key_pstride, int key_digits, int alpha, int L, int N,
                                                          const ModQ *mods) {
     constexpr int V = CKKS_MAC_VEC;

@@ -90,7 +90,7 @@ struct MacTarget {                       // one accumulator limb x of product `j
 
 cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st);
 // vec2: every entry's pointers are 16-byte aligned and its strides even
-// (tensor_job_vec2), so tuples of up to 4 terms may take two coefficients
+// (tensor_job_vec2), so tuples of up to 5 terms may take two coefficients
 // per thread
 bool tensor_job_vec2(const TensorJob &T);
 cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_jobs, int maxt, int max_level,
