@@ -50,6 +50,15 @@ CONFIG = {
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "traffic.json")
 
 
+PRIMES = {"chain": "the largest primes below 2^50 / 2^60 that are 1 mod 2^17 (the default reading)",
+          "q1": "the largest primes below 2^50 / 2^60 that are 1 mod 2^32 (cheaper modular-product forms)"}
+
+
+def congruence(args) -> int:
+    import synth
+    return synth.Q1_CONGRUENCE if args.primes == "q1" else synth.NTT_CONGRUENCE
+
+
 def reduce_max(value: float, world: int, device=None) -> float:
     """Largest value over the ranks (the slowest rank's time); identity for
     one rank. Works with any initialised process group (nccl or gloo)."""
@@ -140,7 +149,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    params = synth.params_large()
+    params = synth.params_large(congruence=congruence(args))
     N, L, K = params.N, params.L, params.K
     ks = [int(x) for x in args.ks.split(",")] if args.ks else KS
     B = args.batch
@@ -354,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded uniform residues, seeded key draws)",
-        "config": dict(CONFIG, ks=ks, batch_per_k=B, products_per_step=B * len(ks),
+        "config": dict(CONFIG, ks=ks, batch_per_k=B, products_per_step=B * len(ks), primes=PRIMES[args.primes],
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                        executor=("one cross-shape wave per step (every stage of all products one launch)"
                                  if args.engine == "waves" else
@@ -748,10 +757,10 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
 # ---------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
-def _oracle_setup(k):
+def _oracle_setup(k, args):
     import synth
     from oracle import ckks as O
-    params = synth.params_large()
+    params = synth.params_large(congruence=congruence(args))
     octx = O.Ctx(params)
     km = synth.key_material(params, k, 3)
     keys = O.keygen_all(octx, km, k)
@@ -769,7 +778,7 @@ def oracle_product_seconds(octx, keys, cts) -> float:
 def cpu_baseline(args):
     from oracle import ring
     k = 4
-    octx, keys, cts = _oracle_setup(k)
+    octx, keys, cts = _oracle_setup(k, args)
     sec = oracle_product_seconds(octx, keys, cts)
     return {"value": round(1.0 / sec, 4), "unit": UNIT, "cores": ring.num_threads(), "kind": "oracle",
             "sample": f"one full-size k={k} product (N=2^16, L=24, K=8, dnum=3) of the step's 144; "
@@ -781,7 +790,7 @@ def run_reference(args, rank, world):
         return None
     from oracle import ring
     k = 4
-    octx, keys, cts = _oracle_setup(k)
+    octx, keys, cts = _oracle_setup(k, args)
     for _ in range(min(args.warmup, 1)):
         oracle_product_seconds(octx, keys, cts)
     times = []
@@ -797,7 +806,8 @@ def run_reference(args, rank, world):
             "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": round(sec * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded uniform residues, seeded key draws)",
-            "config": dict(CONFIG, reference_step="one full-size k=4 product (the cheapest k of the step)"),
+            "config": dict(CONFIG, primes=PRIMES[args.primes],
+                           reference_step="one full-size k=4 product (the cheapest k of the step)"),
             "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": ring.num_threads(),
                              "sample": "one full-size k=4 product per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -847,6 +857,8 @@ def main():
     ap.add_argument("--e2e-engine", default="batch", choices=["batch", "waves"],
                     help="engine of the host-buffer leg: one batched call per k (uploads of each k overlap the "
                          "multiplies of the others) or one wave per step over two alternating buffer sets")
+    ap.add_argument("--primes", default="chain", choices=sorted(PRIMES),
+                    help="prime chain of the workload: " + "; ".join(f"{k}: {v}" for k, v in PRIMES.items()))
     ap.add_argument("--engine", default="waves", choices=["batch", "waves"],
                     help="batch: one batched call per k; waves: the whole step as one cross-shape wave")
     args = ap.parse_args()

@@ -42,6 +42,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--tune", action="append", default=[], help="key=value library tunable")
     ap.add_argument("--partition", default=None, help="partition text for --op mul_k (default Table II)")
+    ap.add_argument("--primes", default="chain", choices=["chain", "q1"],
+                    help="chain: the largest primes of each size that are 1 mod 2^17 (default); q1: primes = 1 "
+                         "mod 2^32, for which the kernels take cheaper modular-product forms")
     ap.add_argument("--params", default="large", choices=["large", "mid", "small"],
                     help="large: 24 x 50-bit q, 8 x 60-bit p, dnum 3; mid: q_0 60-bit + 11 x 45-bit, 4 x 60-bit p, "
                          "dnum 3; small: 4 x 50-bit q, one 60-bit p, dnum 1")
@@ -62,12 +65,13 @@ def main():
         return tensor_rates(args)
     if args.op == "h2d":
         return h2d(args)
+    cong = synth.Q1_CONGRUENCE if args.primes == "q1" else synth.NTT_CONGRUENCE
     if args.params == "small":
-        p = synth.params_small(log_n=args.log_n)
+        p = synth.params_small(log_n=args.log_n, congruence=cong)
     elif args.params == "mid":
-        p = synth.params_mid(log_n=args.log_n)
+        p = synth.params_mid(log_n=args.log_n, congruence=cong)
     else:
-        p = synth.params_large(log_n=args.log_n)
+        p = synth.params_large(log_n=args.log_n, congruence=cong)
     ctx = G.Context.from_params(p)
     L, N, B = p.L, p.N, args.batch
     for kv in args.tune:

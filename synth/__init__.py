@@ -66,9 +66,9 @@ def is_prime(n: int) -> bool:
 
 NTT_CONGRUENCE = 1 << 17  # q = 1 mod 2^17 serves every N <= 2^16
 # q = 1 mod 2^32 (q = h 2^32 + 1): still NTT-friendly for every N <= 2^31, and
-# the modular products of the GPU kernels take a cheaper form for it. The
-# named workloads below use such primes; make_params keeps 2^17 by default so
-# that the general forms stay exercised.
+# the modular products of the GPU kernels take a cheaper form for it. Every
+# parameter set below takes congruence=Q1_CONGRUENCE to use such primes; the
+# default is the 2^17 chain.
 Q1_CONGRUENCE = 1 << 32
 
 
@@ -130,17 +130,17 @@ def make_params(log_n: int, q_bits, k_special: int, dnum: int, p_bits: int = 60,
 
 
 # The five workloads (sizes from the paper's 3-input and k-input settings).
-def params_small(log_n=10, dnum=1, congruence=Q1_CONGRUENCE):
+def params_small(log_n=10, dnum=1, congruence=NTT_CONGRUENCE):
     """4 x 50-bit Q primes, one 60-bit special prime."""
     return make_params(log_n, [50] * 4, 1, dnum, congruence=congruence)
 
 
-def params_mid(log_n=14, congruence=Q1_CONGRUENCE):
+def params_mid(log_n=14, congruence=NTT_CONGRUENCE):
     """12 Q primes (q_0 60-bit, q_1..q_11 45-bit), 4 x 60-bit special, dnum 3."""
     return make_params(log_n, [60] + [45] * 11, 4, 3, congruence=congruence)
 
 
-def params_large(log_n=16, L=24, K=8, dnum=3, congruence=Q1_CONGRUENCE):
+def params_large(log_n=16, L=24, K=8, dnum=3, congruence=NTT_CONGRUENCE):
     """24 x 50-bit Q primes, 8 x 60-bit special primes, dnum 3."""
     return make_params(log_n, [50] * L, K, dnum, congruence=congruence)
 

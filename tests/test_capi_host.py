@@ -151,19 +151,24 @@ def test_precision_criterion_minimises_inner_degree():
 
 
 def test_workload_primes_and_peak_form_check(L):
-    """The named workloads use primes = 1 (mod 2^32), the form the kernels'
+    """The named workloads take the prime chain of the default reading (the
+    largest primes below 2^b that are 1 mod 2^17), or with
+    congruence=Q1_CONGRUENCE primes = 1 (mod 2^32), the form the kernels'
     cheaper modular products need (q = h 2^32 + 1 stays NTT-friendly for
-    every N <= 2^31); make_params keeps the general form by default. The
-    integer-peak entry point rejects the cheaper-form kinds for any other
-    prime before it launches anything."""
+    every N <= 2^31). The integer-peak entry point rejects the cheaper-form
+    kinds for any other prime before it launches anything."""
     import synth
-    for params in (synth.params_small(), synth.params_mid(), synth.params_large()):
-        for x in params.q + params.p:
-            assert x % synth.Q1_CONGRUENCE == 1 and synth.is_prime(x)
-            assert (x - 1) % (2 * params.N) == 0
-        assert len(set(params.q + params.p)) == params.L + params.K
+    for f in (synth.params_small, synth.params_mid, synth.params_large):
+        chain, q1 = f(), f(congruence=synth.Q1_CONGRUENCE)
+        for params, m in ((chain, synth.NTT_CONGRUENCE), (q1, synth.Q1_CONGRUENCE)):
+            for x in params.q + params.p:
+                assert x % m == 1 and synth.is_prime(x)
+                assert (x - 1) % (2 * params.N) == 0
+            assert len(set(params.q + params.p)) == params.L + params.K
+        # the default chain is the largest such primes, so it is not the q1 one
+        assert any(x % synth.Q1_CONGRUENCE != 1 for x in chain.q + chain.p)
+        assert [x.bit_length() for x in chain.q] == [x.bit_length() for x in q1.q]
     general = synth.make_params(10, [50] * 4, 1, 1)
-    assert any(x % synth.Q1_CONGRUENCE != 1 for x in general.q + general.p)
     chains = L.ckks_peak_chains()
     w = (ctypes.c_uint64 * chains)(*([1] * chains))
     q = general.q[0]

@@ -51,7 +51,7 @@ def _product(S, k, seed):
 
 @pytest.mark.parametrize("log_n,ks", [(10, (2, 3, 5, 8, 12)), (14, (3, 12)), (16, (4, 9))])
 def test_cheaper_forms_match_oracle_and_general_forms(log_n, ks):
-    S = Setup(synth.params_large(log_n), max(ks), 7)
+    S = Setup(synth.params_large(log_n, congruence=synth.Q1_CONGRUENCE), max(ks), 7)
     for k in ks:
         cheap, general, want = _product(S, k, 0x9100 + 16 * log_n + k)
         assert np.array_equal(cheap[0], want), f"N=2^{log_n} k={k}: cheaper forms differ from the oracle"
@@ -60,9 +60,9 @@ def test_cheaper_forms_match_oracle_and_general_forms(log_n, ks):
 
 @pytest.mark.parametrize("log_n,k", [(14, 7), (16, 12)])
 def test_general_primes_full_parameter_set(log_n, k):
-    """Primes = 1 (mod 2^17) only: the specialised NTT kernels in the general
-    form at the bench's parameter shape."""
-    params = synth.params_large(log_n, congruence=synth.NTT_CONGRUENCE)
+    """The default prime chain (= 1 mod 2^17 only): the specialised NTT
+    kernels in the general form at the bench's parameter shape."""
+    params = synth.params_large(log_n)
     assert any(x % synth.Q1_CONGRUENCE != 1 for x in params.q + params.p)
     S = Setup(params, k, 8)
     cheap, general, want = _product(S, k, 0x9200 + 16 * log_n + k)
