@@ -359,6 +359,11 @@ __device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS, LOGN> &la
     }
 }
 
+// Staged stores that read an aux limb gather eight elements at a time.
+#ifndef CKKS_NTT_STORE_BATCH
+#define CKKS_NTT_STORE_BATCH 1
+#endif
+
 // One tile (CTA) of one limb: tile index `tile` of the phase.
 template <int LOGN, bool FWD, bool COLS, int LM, int SM, bool Q1>
 __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulonglong2 *tw, u64 q,
@@ -409,11 +414,42 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
     run_passes<LOGN, FWD, COLS, LM, SM, Q1, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
     if (!gout) {
         // shared -> global with the fused store (coalesced)
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int sp, k, e;
-            if (COLS) { k = idx >> lsub; sp = idx & (n_sub - 1); e = t0 + sp + (k << P.log_n2); }
-            else { sp = idx >> LOGN; k = idx & (n - 1); e = ((t0 + sp) << LOGN) + k; }
-            store_elem<SM, Q1>(sc, e, sm[lay.off(sp, k)], FWD);
+        if constexpr (CKKS_NTT_STORE_BATCH && (SM == ST_MRS || SM == ST_ADDSUB)) {
+            // the store reads an aux limb: gather eight elements and their
+            // aux words first, so that eight loads are in flight per thread
+            constexpr int U = 8;
+            for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+                u64 v[U], a[U], a2[U];
+                int e[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int idx = base + u * blockDim.x;
+                    e[u] = -1;
+                    if (idx < total) {
+                        int sp, k;
+                        if (COLS) { k = idx >> lsub; sp = idx & (n_sub - 1); e[u] = t0 + sp + (k << P.log_n2); }
+                        else { sp = idx >> LOGN; k = idx & (n - 1); e[u] = ((t0 + sp) << LOGN) + k; }
+                        v[u] = sm[lay.off(sp, k)];
+                        a[u] = sc.aux[e[u]];
+                        if (SM == ST_ADDSUB) a2[u] = sc.aux2[e[u]];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (e[u] < 0) continue;
+                    const u64 q = sc.m.q;
+                    const u64 r = FWD ? reduce4(v[u], q) : reduce2(v[u], q);
+                    if (SM == ST_MRS) sc.dst[e[u]] = sub_mod(shoup_t<Q1>(a[u], sc.c.w, sc.c.wp, q), r, q);
+                    else sc.dst[e[u]] = sub_mod(add_mod(a[u], a2[u], q), r, q);
+                }
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+                int sp, k, e;
+                if (COLS) { k = idx >> lsub; sp = idx & (n_sub - 1); e = t0 + sp + (k << P.log_n2); }
+                else { sp = idx >> LOGN; k = idx & (n - 1); e = ((t0 + sp) << LOGN) + k; }
+                store_elem<SM, Q1>(sc, e, sm[lay.off(sp, k)], FWD);
+            }
         }
     }
 }
@@ -463,9 +499,6 @@ struct PhaseLaunch {
 #endif
 #ifndef CKKS_NTT_FAST_MINB
 #define CKKS_NTT_FAST_MINB 3    // fixed modes: 80 registers, three CTAs per SM
-#endif
-#ifndef CKKS_NTT_COLS_MINB
-#define CKKS_NTT_COLS_MINB CKKS_NTT_FAST_MINB   // fixed-mode column phases
 #endif
 #ifndef CKKS_NTT_EQ17_MINB
 #define CKKS_NTT_EQ17_MINB 3    // the Eq. 17 load spills a little at 80 registers; three CTAs per SM
@@ -524,7 +557,7 @@ static inline cudaError_t dispatch_fast(bool cols, int logn, const NttPhase &P, 
     if (logn == LG) {                                                                              \
         if constexpr (FWD) {                                                                       \
             if (cols && S.mode == ST_LAZY) {                                                       \
-                if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_LAZY, CKKS_NTT_COLS_MINB, Q1); \
+                if (L.mode == LD_PLAIN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_LAZY, CKKS_NTT_FAST_MINB, Q1); \
                 if (L.mode == LD_EQ17) CKKS_LAUNCH(LG, true, LD_EQ17, ST_LAZY, CKKS_NTT_EQ17_MINB, Q1);   \
             }                                                                                      \
             if (!cols && L.mode == LD_PLAIN) {                                                     \
@@ -537,8 +570,8 @@ static inline cudaError_t dispatch_fast(bool cols, int logn, const NttPhase &P, 
                 if (L.mode == LD_ADD) CKKS_LAUNCH(LG, false, LD_ADD, ST_LAZY, CKKS_NTT_FAST_MINB, Q1);    \
             }                                                                                      \
             if (cols && L.mode == LD_PLAIN) {                                                      \
-                if (S.mode == ST_SCALE) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_SCALE, CKKS_NTT_COLS_MINB, Q1); \
-                if (S.mode == ST_MODDOWN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_MODDOWN, CKKS_NTT_COLS_MINB, Q1); \
+                if (S.mode == ST_SCALE) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_SCALE, CKKS_NTT_FAST_MINB, Q1); \
+                if (S.mode == ST_MODDOWN) CKKS_LAUNCH(LG, true, LD_PLAIN, ST_MODDOWN, CKKS_NTT_FAST_MINB, Q1); \
             }                                                                                      \
         }                                                                                          \
     }
