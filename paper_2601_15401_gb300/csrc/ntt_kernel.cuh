@@ -257,6 +257,15 @@ __device__ __forceinline__ void store_elem(const StoreCtx &c, int e, u64 v, bool
     }
 }
 
+// Fused loads / stores that sum over several limbs (the Eq. 17 load, the
+// ModDown store) issue the loads of several elements together.
+#ifndef CKKS_NTT_EQ17_BY_TERM
+#define CKKS_NTT_EQ17_BY_TERM 1
+#endif
+#ifndef CKKS_NTT_MODDOWN_GROUPS
+#define CKKS_NTT_MODDOWN_GROUPS 1
+#endif
+
 // One pass of R stages starting at local stage E0 on every point set of the
 // tile. GIN / GOUT: the pass reads / writes global memory (fused load /
 // store) instead of shared memory.
@@ -277,14 +286,42 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
         const int g = set / t_min;
         const int base = g * 2 * t0s + o;
         u64 x[EL];
+        if constexpr (CKKS_NTT_EQ17_BY_TERM && GIN && LM == LD_EQ17) {
+            // Eq. 17 combination term by term: the EL loads of one term are
+            // in flight together (the per-element loop over the terms had
+            // one load in flight per thread)
+            const u64 q = lc.m.q;
 #pragma unroll
-        for (int k = 0; k < EL; ++k) {
-            const int pt = base + k * t_min;
-            if (GIN) {
-                const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
-                x[k] = load_elem<LM, Q1>(lc, e);
-            } else {
-                x[k] = sm[lay.off(sp, pt)];
+            for (int k = 0; k < EL; ++k) x[k] = 0;
+            for (int t = 0; t < lc.mu; ++t) {
+                const Shoup g = lc.g[t];
+                const u64 *bt = lc.b + (i64)t * lc.N;
+#pragma unroll
+                for (int k = 0; k < EL; ++k) {
+                    const int pt = base + k * t_min;
+                    const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
+                    x[k] = add_mod(x[k], shoup_t<Q1>(bt[e], g.w, g.wp, q), q);
+                }
+            }
+            if (lc.with_self) {
+                const Shoup g = lc.g[lc.mu];
+#pragma unroll
+                for (int k = 0; k < EL; ++k) {
+                    const int pt = base + k * t_min;
+                    const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
+                    x[k] = sub_mod(shoup_t<Q1>(lc.a[e], g.w, g.wp, q), x[k], q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < EL; ++k) {
+                const int pt = base + k * t_min;
+                if (GIN) {
+                    const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
+                    x[k] = load_elem<LM, Q1>(lc, e);
+                } else {
+                    x[k] = sm[lay.off(sp, pt)];
+                }
             }
         }
         const int twb = tw_b0 + tw_bmul * sp;
@@ -315,14 +352,45 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
                 }
             }
         }
+        if constexpr (CKKS_NTT_MODDOWN_GROUPS && GOUT && SM == ST_MODDOWN) {
+            // ModDown store (Eq. 5 with Eq. 11 / 12) four elements at a time,
+            // their K z-limb loads in flight together
+            const u64 q = sc.m.q;
+            constexpr int G4 = EL >= 4 ? 4 : EL;
 #pragma unroll
-        for (int k = 0; k < EL; ++k) {
-            const int pt = base + k * t_min;
-            if (GOUT) {
-                const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
-                store_elem<SM, Q1>(sc, e, x[k], FWD);
-            } else {
-                sm[lay.off(sp, pt)] = x[k];
+            for (int k0 = 0; k0 < EL; k0 += G4) {
+                int e[G4];
+                Acc128Lazy acc[G4];  // sum of the P primes < 2^64 (context check)
+#pragma unroll
+                for (int u = 0; u < G4; ++u) {
+                    const int pt = base + (k0 + u) * t_min;
+                    e[u] = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
+                    acc[u].zero();
+                }
+                for (int i = 0; i < sc.K; ++i) {
+                    const u64 c = sc.cK[i];
+                    const u64 *zi = sc.aux + (i64)i * sc.N;
+                    u64 z[G4];
+#pragma unroll
+                    for (int u = 0; u < G4; ++u) z[u] = zi[e[u]];
+#pragma unroll
+                    for (int u = 0; u < G4; ++u) acc[u].mac(z[u], c);
+                }
+#pragma unroll
+                for (int u = 0; u < G4; ++u)
+                    sc.dst[e[u]] = sub_mod(shoup_t<Q1>(x[k0 + u], sc.c.w, sc.c.wp, q),
+                                           redc_t<Q1>(acc[u].hi, acc[u].lo, sc.m), q);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < EL; ++k) {
+                const int pt = base + k * t_min;
+                if (GOUT) {
+                    const int e = COLS ? t0 + sp + (pt << log_n2) : ((t0 + sp) << LOGN) + pt;
+                    store_elem<SM, Q1>(sc, e, x[k], FWD);
+                } else {
+                    sm[lay.off(sp, pt)] = x[k];
+                }
             }
         }
     }
