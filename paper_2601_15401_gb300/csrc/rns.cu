@@ -499,51 +499,6 @@ __device__ __forceinline__ void mac_span(const u64 *dsrc, i64 dstride, const u64
         a0[v].zero();
         a1[v].zero();
     }
-#if CKKS_MAC_PIPE
-    // software-pipelined over the (t, beta) terms: the next term's three
-    // loads are issued before this term's multiply-adds
-    const int terms = (n - 1) * nd;
-    int t = 2, beta = 0;
-    auto term_ptrs = [&](int tt, int bb, const u64 *&src, const u64 *&key) {
-        src = bb == my_digit ? dsrc + (i64)tt * dstride : esrc + (i64)((tt - 2) * nd + bb) * estride;
-        key = krow + ((i64)((tt - 2) * key_digits + bb) * 2) * key_pstride;
-    };
-    u64 tv[V], k0[V], k1[V];
-    {
-        const u64 *src, *key;
-        term_ptrs(t, beta, src, key);
-        load_span<V>(src, tv);
-        load_span<V>(key, k0);
-        load_span<V>(key + key_pstride, k1);
-    }
-    for (int j = 0; j < terms; ++j) {
-        if (++beta == nd) {
-            beta = 0;
-            ++t;
-        }
-        u64 ntv[V], nk0[V], nk1[V];
-        if (j + 1 < terms) {
-            const u64 *src, *key;
-            term_ptrs(t, beta, src, key);
-            load_span<V>(src, ntv);
-            load_span<V>(key, nk0);
-            load_span<V>(key + key_pstride, nk1);
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            a0[v].mac(tv[v], k0[v], q);
-            a1[v].mac(tv[v], k1[v], q);
-        }
-        if (j + 1 < terms) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                tv[v] = ntv[v];
-                k0[v] = nk0[v];
-                k1[v] = nk1[v];
-            }
-        }
-    }
-#else
     for (int t = 2; t <= n; ++t) {
         for (int beta = 0; beta < nd; ++beta) {
             const u64 *src = beta == my_digit ? dsrc + (i64)t * dstride : esrc + (i64)((t - 2) * nd + beta) * estride;
@@ -559,7 +514,6 @@ __device__ __forceinline__ void mac_span(const u64 *dsrc, i64 dstride, const u64
             }
         }
     }
-#endif
     u64 r0[V], r1[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
