@@ -32,7 +32,7 @@ static int phase_geometry(const Context &C, bool cols, NttPhase &P, PhaseLaunch 
         n_sub = C.tune_ntt_tile_cols / n;
         if (n_sub > P.N2) n_sub = P.N2;
         G.tiles = P.N2 / n_sub;
-        G.smem = (size_t)n * n_sub * sizeof(u64);
+        G.smem = (size_t)n * n_sub * sizeof(u64) + (CKKS_NTT_COL_TW_SMEM ? (size_t)n * sizeof(ulonglong2) : 0);
     } else {
         logn = log_n2;
         int n = 1 << logn;

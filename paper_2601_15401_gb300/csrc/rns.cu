@@ -331,6 +331,11 @@ cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_j
 #ifndef CKKS_MAC_VEC
 #define CKKS_MAC_VEC 4
 #endif
+// Two products of the same shape per thread share each term's key loads
+// (CKKS_MAC_PAIR, rns.h), two coefficients each.
+#ifndef CKKS_MAC_VEC_PAIR
+#define CKKS_MAC_VEC_PAIR 2
+#endif
 // Largest key-MAC block (the "mac_threads" tunable's upper bound). At 1024
 // the four-coefficient form gets 64 registers and spills 96-196 bytes a
 // thread to L1; bounding the block at 512 removed the spills (106
@@ -488,51 +493,68 @@ cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_job
 // V coefficients of accumulator limb x of one product: dsrc / esrc point at
 // limb x, coefficient e of the D tuple / the first ModUp output; krow at the
 // prime's row, coefficient e, of the first key.
-template <int V, bool Q1>
-__device__ __forceinline__ void mac_span(const u64 *dsrc, i64 dstride, const u64 *esrc, i64 estride, int n, int nd,
-                                         int my_digit, const u64 *krow, i64 key_pstride, int key_digits, const ModQ m,
-                                         u64 *dst, i64 astride) {
+// V coefficients of accumulator limb x of P products of the same shape
+// (level, n, digits) at once: the key words of each term are loaded once
+// for all P. dsrc / esrc point at limb x, coefficient e of each product's D
+// tuple / first ModUp output; krow at the prime's row, coefficient e, of the
+// first key.
+template <int V, int P, bool Q1>
+__device__ __forceinline__ void mac_span(const u64 *const *dsrc, const i64 *dstride, const u64 *const *esrc,
+                                         const i64 *estride, int n, int nd, int my_digit, const u64 *krow,
+                                         i64 key_pstride, int key_digits, const ModQ m, u64 *const *dst,
+                                         const i64 *astride) {
     const u64 q = m.q;
-    Acc128 a0[V], a1[V];
+    Acc128 a0[P][V], a1[P][V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        a0[v].zero();
-        a1[v].zero();
-    }
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            a0[p][v].zero();
+            a1[p][v].zero();
+        }
     for (int t = 2; t <= n; ++t) {
         for (int beta = 0; beta < nd; ++beta) {
-            const u64 *src = beta == my_digit ? dsrc + (i64)t * dstride : esrc + (i64)((t - 2) * nd + beta) * estride;
             const u64 *key = krow + ((i64)((t - 2) * key_digits + beta) * 2) * key_pstride;
-            u64 tv[V], k0[V], k1[V];
-            load_span<V>(src, tv);
+            u64 tv[P][V], k0[V], k1[V];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const u64 *src = beta == my_digit ? dsrc[p] + (i64)t * dstride[p]
+                                                  : esrc[p] + (i64)((t - 2) * nd + beta) * estride[p];
+                load_span<V>(src, tv[p]);
+            }
             load_span<V>(key, k0);
             load_span<V>(key + key_pstride, k1);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                a0[v].mac(tv[v], k0[v], q);
-                a1[v].mac(tv[v], k1[v], q);
-            }
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    a0[p][v].mac(tv[p][v], k0[v], q);
+                    a1[p][v].mac(tv[p][v], k1[v], q);
+                }
         }
     }
-    u64 r0[V], r1[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        r0[v] = redc_t<Q1>(a0[v].hi, a0[v].lo, m);
-        r1[v] = redc_t<Q1>(a1[v].hi, a1[v].lo, m);
+    for (int p = 0; p < P; ++p) {
+        u64 r0[V], r1[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            r0[v] = redc_t<Q1>(a0[p][v].hi, a0[p][v].lo, m);
+            r1[v] = redc_t<Q1>(a1[p][v].hi, a1[p][v].lo, m);
+        }
+        store_span<V>(dst[p], r0);
+        store_span<V>(dst[p] + astride[p], r1);
     }
-    store_span<V>(dst, r0);
-    store_span<V>(dst + astride, r1);
 }
 
-template <bool Q1>
-__global__ void __launch_bounds__(CKKS_MAC_MAX_THREADS) mac_kernel(MacArgs A) {
-    constexpr int V = CKKS_MAC_VEC;
+// Batch elements b_first + g P + p (p < P) of group g; blockIdx.x runs over
+// groups fastest, then coefficient chunks, then accumulator limbs, so that
+// blocks that share key rows run next to each other.
+template <bool Q1, int P, int V>
+__global__ void __launch_bounds__(CKKS_MAC_MAX_THREADS) mac_kernel(MacArgs A, int b_first, int n_groups) {
     const int chunks = (A.N + blockDim.x * V - 1) / (blockDim.x * V);
-    // block order: batch fastest, then chunk, then limb -> blocks that share a
-    // key tile run next to each other
     int bid = blockIdx.x;
-    const int b = bid % A.n_batch;
-    bid /= A.n_batch;
+    const int g = bid % n_groups;
+    bid /= n_groups;
     const int chunk = bid % chunks;
     const int x = bid / chunks;  // acc slot: Q limbs 0..level-1 then P limbs
     const int e = (chunk * blockDim.x + threadIdx.x) * V;
@@ -540,16 +562,34 @@ __global__ void __launch_bounds__(CKKS_MAC_MAX_THREADS) mac_kernel(MacArgs A) {
     const bool isq = x < A.level;
     const int prime = isq ? x : A.L + (x - A.level);
     const i64 off = (i64)x * A.N + e;
-    mac_span<V, Q1>(A.d.ptr + (i64)b * A.d.bstride + off, A.d.pstride, A.ext.ptr + (i64)b * A.ext.bstride + off,
-                A.ext.pstride, A.n, A.n_digits, isq ? x / A.alpha : -1, A.keys + (i64)prime * A.N + e, A.key_pstride,
-                A.key_digits, A.mods[prime], A.acc.ptr + (i64)b * A.acc.bstride + off, A.acc.pstride);
+    const u64 *ds[P], *es[P];
+    u64 *os[P];
+    i64 dstr[P], estr[P], astr[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const i64 b = b_first + (i64)g * P + p;
+        ds[p] = A.d.ptr + b * A.d.bstride + off;
+        es[p] = A.ext.ptr + b * A.ext.bstride + off;
+        os[p] = A.acc.ptr + b * A.acc.bstride + off;
+        dstr[p] = A.d.pstride;
+        estr[p] = A.ext.pstride;
+        astr[p] = A.acc.pstride;
+    }
+    mac_span<V, P, Q1>(ds, dstr, es, estr, A.n, A.n_digits, isq ? x / A.alpha : -1, A.keys + (i64)prime * A.N + e,
+                       A.key_pstride, A.key_digits, A.mods[prime], os, astr);
+}
+
+template <int P, int V>
+static void launch_mac_part(const Context &C, const MacArgs &A, int b_first, int n_groups, cudaStream_t st) {
+    const int thr = C.tune_mac_threads;
+    const int chunks = (A.N + thr * V - 1) / (thr * V);
+    const long long blocks = (long long)chunks * (A.level + A.K) * n_groups;
+    count_kernel(C);
+    if (C.q1()) mac_kernel<true, P, V><<<(unsigned)blocks, thr, 0, st>>>(A, b_first, n_groups);
+    else mac_kernel<false, P, V><<<(unsigned)blocks, thr, 0, st>>>(A, b_first, n_groups);
 }
 
 cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
-    const int thr = C.tune_mac_threads;
-    const int chunks = (A.N + thr * CKKS_MAC_VEC - 1) / (thr * CKKS_MAC_VEC);
-    long long blocks = (long long)chunks * (A.level + A.K) * A.n_batch;
-    count_kernel(C);
     // per batch element: (n-1) * digits terms and 2 outputs per target limb;
     // key limbs counted once per launch
     const double terms = (double)(A.n - 1) * A.n_digits;
@@ -557,47 +597,73 @@ cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st) {
     double bytes = ((terms + 2.0) * A.n_batch + 2.0 * terms) * limbs * A.N * sizeof(u64);
     const double macs = 2.0 * terms * limbs * A.n_batch * A.N;
     ProfScope ps(C, KC_MAC, bytes, st, macs);
-    if (C.q1()) mac_kernel<true><<<(unsigned)blocks, thr, 0, st>>>(A);
-    else mac_kernel<false><<<(unsigned)blocks, thr, 0, st>>>(A);
+    // pairs of batch elements share the key loads; an odd last one alone
+    const int pairs = CKKS_MAC_PAIR ? A.n_batch / 2 : 0;
+    if (pairs > 0) launch_mac_part<2, CKKS_MAC_VEC_PAIR>(C, A, 0, pairs, st);
+    if (A.n_batch - 2 * pairs > 0) launch_mac_part<1, CKKS_MAC_VEC>(C, A, 2 * pairs, A.n_batch - 2 * pairs, st);
     return cudaGetLastError();
 }
 
-// Table launch of the key MAC: blockIdx.x = accumulator limb (product, x),
-// ordered by prime so that neighbouring blocks read the same key rows;
-// blockIdx.y = coefficient chunk.
-template <bool Q1>
-__global__ void __launch_bounds__(CKKS_MAC_MAX_THREADS) mac_table_kernel(const MacJob *jobs, const MacTarget *targets, const u64 *keys,
-                                                         i64 key_pstride, int key_digits, int alpha, int L, int N,
-                                                         const ModQ *mods) {
-    constexpr int V = CKKS_MAC_VEC;
+// Table launch of the key MAC: blockIdx.x = accumulator limb (products
+// job [, job2], x), ordered by prime so that neighbouring blocks read the
+// same key rows; blockIdx.y = coefficient chunk. P = 2: the target pairs
+// two products of the same shape (job2), which share the key loads.
+template <bool Q1, int P, int V>
+__global__ void __launch_bounds__(CKKS_MAC_MAX_THREADS) mac_table_kernel(const MacJob *jobs, const MacTarget *targets,
+                                                                         const u64 *keys, i64 key_pstride,
+                                                                         int key_digits, int alpha, int L, int N,
+                                                                         const ModQ *mods) {
     const MacTarget T = targets[blockIdx.x];
-    const MacJob J = jobs[T.job];
     const int e = (blockIdx.y * blockDim.x + threadIdx.x) * V;
     if (e >= N) return;
     const int x = T.x;
-    const bool isq = x < J.level;
-    const int prime = isq ? x : L + (x - J.level);
+    const MacJob J0 = jobs[T.job];
+    const bool isq = x < J0.level;
+    const int prime = isq ? x : L + (x - J0.level);
     const i64 off = (i64)x * N + e;
-    mac_span<V, Q1>(J.d + off, J.dstride, J.ext + off, J.estride, J.n, J.nd, isq ? x / alpha : -1,
-                keys + (i64)prime * N + e, key_pstride, key_digits, mods[prime], J.acc + off, J.astride);
+    const u64 *ds[P], *es[P];
+    u64 *os[P];
+    i64 dstr[P], estr[P], astr[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const MacJob J = p == 0 ? J0 : jobs[T.job2];
+        ds[p] = J.d + off;
+        es[p] = J.ext + off;
+        os[p] = J.acc + off;
+        dstr[p] = J.dstride;
+        estr[p] = J.estride;
+        astr[p] = J.astride;
+    }
+    mac_span<V, P, Q1>(ds, dstr, es, estr, J0.n, J0.nd, isq ? x / alpha : -1, keys + (i64)prime * N + e, key_pstride,
+                       key_digits, mods[prime], os, astr);
 }
 
-cudaError_t launch_mac_table(const Context &C, const MacJob *jobs, const MacTarget *targets, int n_targets,
-                             const u64 *keys, double bytes, double macs, cudaStream_t st) {
-    if (n_targets <= 0) return cudaSuccess;
+template <int P, int V>
+static cudaError_t launch_mac_table_part(const Context &C, const MacJob *jobs, const MacTarget *targets, int n,
+                                         const u64 *keys, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
     const int thr = C.tune_mac_threads;
-    const int chunks = (C.N + thr * CKKS_MAC_VEC - 1) / (thr * CKKS_MAC_VEC);
+    const int chunks = (C.N + thr * V - 1) / (thr * V);
     if (chunks > 65535) return cudaErrorInvalidValue;
     count_kernel(C);
-    ProfScope ps(C, KC_MAC, bytes, st, macs);
-    dim3 grid((unsigned)n_targets, (unsigned)chunks);
+    dim3 grid((unsigned)n, (unsigned)chunks);
+    const i64 kps = (i64)(C.L + C.K) * C.N;
     if (C.q1())
-        mac_table_kernel<true><<<grid, thr, 0, st>>>(jobs, targets, keys, (i64)(C.L + C.K) * C.N, C.dnum, C.alpha,
-                                                     C.L, C.N, C.d_mods);
+        mac_table_kernel<true, P, V><<<grid, thr, 0, st>>>(jobs, targets, keys, kps, C.dnum, C.alpha, C.L, C.N,
+                                                           C.d_mods);
     else
-        mac_table_kernel<false><<<grid, thr, 0, st>>>(jobs, targets, keys, (i64)(C.L + C.K) * C.N, C.dnum, C.alpha,
-                                                      C.L, C.N, C.d_mods);
+        mac_table_kernel<false, P, V><<<grid, thr, 0, st>>>(jobs, targets, keys, kps, C.dnum, C.alpha, C.L, C.N,
+                                                            C.d_mods);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mac_table(const Context &C, const MacJob *jobs, const MacTarget *targets, int n_pairs,
+                             int n_targets, const u64 *keys, double bytes, double macs, cudaStream_t st) {
+    if (n_targets <= 0) return cudaSuccess;
+    ProfScope ps(C, KC_MAC, bytes, st, macs);
+    cudaError_t e = launch_mac_table_part<2, CKKS_MAC_VEC_PAIR>(C, jobs, targets, n_pairs, keys, st);
+    if (e != cudaSuccess) return e;
+    return launch_mac_table_part<1, CKKS_MAC_VEC>(C, jobs, targets + n_pairs, n_targets - n_pairs, keys, st);
 }
 
 // ---------------------------------------------------------------------------

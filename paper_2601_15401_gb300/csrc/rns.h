@@ -84,8 +84,16 @@ struct MacJob {                          // the key MAC of one product
     int level, n, nd, pad;
 };
 
-struct MacTarget {                       // one accumulator limb x of product `job`
-    int job, x;
+// 1: the key MAC takes two products of the same shape per thread, so that
+// each key word is loaded once for both (the keys were otherwise re-read
+// from L2 for every product: seven times the kernel's DRAM bytes went
+// through L2); 0: one product per thread
+#ifndef CKKS_MAC_PAIR
+#define CKKS_MAC_PAIR 1
+#endif
+
+struct MacTarget {                       // accumulator limb x of product `job` (and of `job2`, of the same
+    int job, x, job2, pad;               // shape, when the target pairs two products; else job2 = -1)
 };
 
 cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st);
@@ -100,8 +108,9 @@ cudaError_t launch_rschain_table(const Context &C, const RsJob *jobs, int n_jobs
                                  cudaStream_t st);
 cudaError_t launch_bconv_table(const Context &C, const BconvJob *jobs, int n_jobs, double bytes, double macs,
                                cudaStream_t st);
-cudaError_t launch_mac_table(const Context &C, const MacJob *jobs, const MacTarget *targets, int n_targets,
-                             const u64 *keys, double bytes, double macs, cudaStream_t st);
+// targets[0 .. n_pairs) pair two products (job2 >= 0), the rest are single
+cudaError_t launch_mac_table(const Context &C, const MacJob *jobs, const MacTarget *targets, int n_pairs,
+                             int n_targets, const u64 *keys, double bytes, double macs, cudaStream_t st);
 cudaError_t launch_bconv(const Context &C, const BconvArgs &A, cudaStream_t st);
 cudaError_t launch_mac(const Context &C, const MacArgs &A, cudaStream_t st);
 cudaError_t launch_rschain(const Context &C, const RsChainArgs &A, cudaStream_t st);

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ckks_mulk.h"
@@ -60,6 +61,7 @@ struct Stage {
     StoreSpec S{};
     int maxt = 0, max_level = 0, max_polys = 0;
     bool vec2 = true;  // tensor: every entry 16-byte aligned with even strides
+    int n_pairs = 0;   // key MAC: targets[0 .. n_pairs) pair two products
     std::vector<NttJob> ntt;
     std::vector<TensorJob> tensor;
     std::vector<RsJob> rs;
@@ -354,7 +356,7 @@ void build_product(Builder &B, const WaveProduct &w, Bump &ws) {
             M.nd = ndig;
             const int job = (int)s.mac.size();
             s.mac.push_back(M);
-            for (int x = 0; x < ext_l; ++x) s.targets.push_back(MacTarget{job, x});
+            for (int x = 0; x < ext_l; ++x) s.targets.push_back(MacTarget{job, x, -1, 0});
             const double terms = (double)(n - 1) * ndig;
             s.bytes += (terms + 2.0) * ext_l * limb;
             s.ops += 2.0 * terms * ext_l * N;
@@ -450,10 +452,33 @@ int build(ckks_wave &W, char *scratch, std::vector<char> &tables) {
         if (s.kind == SK_RSCHAIN) s.off = put(tables, s.rs);
         if (s.kind == SK_BCONV) s.off = put(tables, s.bconv);
         if (s.kind == SK_MAC) {
-            // accumulator limbs ordered by prime: neighbouring blocks share key rows
-            std::stable_sort(s.targets.begin(), s.targets.end(), [&](const MacTarget &a, const MacTarget &b) {
+            // two products of the same shape (level, n, digits) share the key
+            // loads of a limb x: pair their targets, pairs first; each part
+            // ordered by prime, so that neighbouring blocks share key rows
+            std::vector<MacTarget> pairs, singles;
+            {
+                std::map<std::tuple<int, int, int, int>, int> open;  // (level, n, nd, x) -> unpaired target
+                for (const MacTarget &t : s.targets) {
+                    const MacJob &J = s.mac[t.job];
+                    const auto key = std::make_tuple(J.level, J.n, J.nd, t.x);
+                    auto it = open.find(key);
+                    if (CKKS_MAC_PAIR && it != open.end()) {
+                        pairs.push_back(MacTarget{it->second, t.x, t.job, 0});
+                        open.erase(it);
+                    } else {
+                        open[key] = t.job;
+                    }
+                }
+                for (const auto &kv : open) singles.push_back(MacTarget{kv.second, std::get<3>(kv.first), -1, 0});
+            }
+            auto by_prime = [&](const MacTarget &a, const MacTarget &b) {
                 return B.prime_of_slot(a.x, s.mac[a.job].level) < B.prime_of_slot(b.x, s.mac[b.job].level);
-            });
+            };
+            std::stable_sort(pairs.begin(), pairs.end(), by_prime);
+            std::stable_sort(singles.begin(), singles.end(), by_prime);
+            s.n_pairs = (int)pairs.size();
+            s.targets = pairs;
+            s.targets.insert(s.targets.end(), singles.begin(), singles.end());
             s.off = put(tables, s.mac);
             s.off2 = put(tables, s.targets);
         }
@@ -486,8 +511,8 @@ cudaError_t enqueue(ckks_wave &W, char *ws /* the job tables */, cudaStream_t st
             e = launch_bconv_table(C, (const BconvJob *)(ws + s.off), n, s.bytes, s.ops, st);
             break;
         case SK_MAC:
-            e = launch_mac_table(C, (const MacJob *)(ws + s.off), (const MacTarget *)(ws + s.off2), n, W.evk->keys,
-                                 s.bytes, s.ops, st);
+            e = launch_mac_table(C, (const MacJob *)(ws + s.off), (const MacTarget *)(ws + s.off2), s.n_pairs, n,
+                                 W.evk->keys, s.bytes, s.ops, st);
             break;
         }
         if (e != cudaSuccess) return e;
