@@ -461,8 +461,12 @@ int build(ckks_wave &W, char *scratch, std::vector<char> &tables) {
                 for (const MacTarget &t : s.targets) {
                     const MacJob &J = s.mac[t.job];
                     const auto key = std::make_tuple(J.level, J.n, J.nd, t.x);
+                    if (!CKKS_MAC_PAIR) {
+                        singles.push_back(t);
+                        continue;
+                    }
                     auto it = open.find(key);
-                    if (CKKS_MAC_PAIR && it != open.end()) {
+                    if (it != open.end()) {
                         pairs.push_back(MacTarget{it->second, t.x, t.job, 0});
                         open.erase(it);
                     } else {
