@@ -16,7 +16,7 @@ void ntt_geometry(int logN, int &log_n1, int &log_n2) {
 
 // Tile shape of one phase: sub-problems per CTA from the context's tile
 // tunables, CTAs per limb, threads and shared memory per CTA.
-static int phase_geometry(const Context &C, bool fwd, bool cols, NttPhase &P, PhaseLaunch &G) {
+static int phase_geometry(const Context &C, bool cols, NttPhase &P, PhaseLaunch &G) {
     int log_n1, log_n2;
     ntt_geometry(C.log_n, log_n1, log_n2);
     P.N = C.N;
@@ -41,10 +41,6 @@ static int phase_geometry(const Context &C, bool fwd, bool cols, NttPhase &P, Ph
         if (n_sub > P.N1) n_sub = P.N1;
         G.tiles = P.N1 / n_sub;
         G.smem = (size_t)n_sub * (n + n / 16) * sizeof(u64);
-        // forward block phases with two passes: the second pass's twiddles
-        // staged behind the tile (n_sub (n - 2^ceil(logn/2)) pairs)
-        if (CKKS_NTT_BLK_TW_SMEM && fwd && logn >= 5 && logn <= 8)
-            G.smem += (size_t)n_sub * (n - (1 << ((logn + 1) / 2))) * sizeof(ulonglong2);
     }
     P.sub_per_tile = n_sub;
     P.log_sub = 0;
@@ -63,7 +59,7 @@ cudaError_t launch_ntt_phase(const Context &C, bool fwd, bool cols, const LimbJo
                              const StoreSpec &S, cudaStream_t st) {
     NttPhase P;
     PhaseLaunch G;
-    const int logn = phase_geometry(C, fwd, cols, P, G);
+    const int logn = phase_geometry(C, cols, P, G);
     G.st = st;
     count_op(C, fwd ? OP_NTT_PHASE : OP_INTT_PHASE);
     count_kernel(C);
@@ -105,7 +101,7 @@ cudaError_t launch_ntt_phase_table(const Context &C, bool fwd, bool cols, const 
     if (n_jobs <= 0) return cudaSuccess;
     NttPhase P;
     PhaseLaunch G;
-    const int logn = phase_geometry(C, fwd, cols, P, G);
+    const int logn = phase_geometry(C, cols, P, G);
     G.st = st;
     count_op(C, fwd ? OP_NTT_PHASE : OP_INTT_PHASE);
     count_kernel(C);

@@ -269,10 +269,10 @@ __device__ __forceinline__ void store_elem(const StoreCtx &c, int e, u64 v, bool
 // One pass of R stages starting at local stage E0 on every point set of the
 // tile. GIN / GOUT: the pass reads / writes global memory (fused load /
 // store) instead of shared memory.
-template <int LOGN, int R, int E0, bool FWD, bool COLS, bool GIN, bool GOUT, int LM, int SM, bool Q1, bool TWS>
+template <int LOGN, int R, int E0, bool FWD, bool COLS, bool GIN, bool GOUT, int LM, int SM, bool Q1>
 __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay, const ulonglong2 *tw, int tw_b0,
                                          int tw_bmul, u64 q, const LoadCtx &lc, const StoreCtx &sc, int t0,
-                                         int log_n2, const ulonglong2 *tws) {
+                                         int log_n2) {
     constexpr int n = 1 << LOGN;
     constexpr int EL = 1 << R;
     constexpr int t_min = n >> (E0 + R);
@@ -334,8 +334,7 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
                 for (int k = 0; k < EL; ++k) {
                     if ((k & h) == 0) {
                         const int i = (g << ep) + (k >> (R - ep));
-                        const ulonglong2 w = TWS ? tws[((m - (1 << E0)) << lay.lsub) + m * sp + i] : tw[m * twb + i];
-                        ct_bfly<Q1>(x[k], x[k + h], w, q);
+                        ct_bfly<Q1>(x[k], x[k + h], tw[m * twb + i], q);
                     }
                 }
             }
@@ -348,8 +347,7 @@ __device__ __forceinline__ void run_pass(u64 *sm, const Layout<COLS, LOGN> &lay,
                 for (int k = 0; k < EL; ++k) {
                     if ((k & h) == 0) {
                         const int i = (g << ep) + (k >> (R - ep));
-                        const ulonglong2 w = TWS ? tws[((m - (1 << E0)) << lay.lsub) + m * sp + i] : tw[m * twb + i];
-                        gs_bfly<Q1>(x[k], x[k + h], w, q);
+                        gs_bfly<Q1>(x[k], x[k + h], tw[m * twb + i], q);
                     }
                 }
             }
@@ -412,36 +410,20 @@ struct PassAccess {
     static constexpr bool direct_in = direct && CKKS_NTT_DIRECT_IN;
 };
 
-// Forward block phases with two passes can copy the second pass's twiddles
-// (per block distinct: n_sub (n - 2^start) pairs per tile) into shared memory
-// with cp.async while the first pass runs (CKKS_NTT_BLK_TW_SMEM).
-#ifndef CKKS_NTT_BLK_TW_SMEM
-#define CKKS_NTT_BLK_TW_SMEM 0
-#endif
-template <int LOGN, bool FWD, bool COLS>
-struct BlockTwStage {
-    static constexpr bool on = CKKS_NTT_BLK_TW_SMEM && FWD && !COLS && Pass<LOGN, 0>::NP == 2;
-    static constexpr int m0 = 1 << Pass<LOGN, 1>::start;  // first staged stage's group count
-};
-
 template <int LOGN, bool FWD, bool COLS, int LM, int SM, bool Q1, int I>
 __device__ __forceinline__ void run_passes(u64 *sm, const Layout<COLS, LOGN> &lay, const ulonglong2 *tw, int tw_b0,
                                            int tw_bmul, u64 q, const LoadCtx &lc, const StoreCtx &sc, int t0,
-                                           int log_n2, const ulonglong2 *tws) {
+                                           int log_n2) {
     constexpr int NP = Pass<LOGN, 0>::NP;
     if constexpr (I < NP) {
         constexpr int PP = FWD ? I : NP - 1 - I;
         constexpr bool first = I == 0, last = I == NP - 1;
         constexpr bool gin = first && PassAccess<LOGN, COLS, PP>::direct_in;
         constexpr bool gout = last && PassAccess<LOGN, COLS, PP>::direct;
-        constexpr bool staged = BlockTwStage<LOGN, FWD, COLS>::on && PP == 1;
-        run_pass<LOGN, Pass<LOGN, PP>::len, Pass<LOGN, PP>::start, FWD, COLS, gin, gout, LM, SM, Q1, staged>(
-            sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2, tws);
-        if (!last || !gout) {
-            if constexpr (BlockTwStage<LOGN, FWD, COLS>::on && I == 0) asm volatile("cp.async.wait_all;\n" ::: "memory");
-            __syncthreads();
-        }
-        run_passes<LOGN, FWD, COLS, LM, SM, Q1, I + 1>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2, tws);
+        run_pass<LOGN, Pass<LOGN, PP>::len, Pass<LOGN, PP>::start, FWD, COLS, gin, gout, LM, SM, Q1>(
+            sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
+        if (!last || !gout) __syncthreads();
+        run_passes<LOGN, FWD, COLS, LM, SM, Q1, I + 1>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, log_n2);
     }
 }
 
@@ -512,26 +494,7 @@ __device__ __forceinline__ void phase_tile(u64 *sm, const NttPhase &P, const ulo
         }
         __syncthreads();
     }
-    const ulonglong2 *tws = nullptr;
-    if constexpr (BlockTwStage<LOGN, FWD, COLS>::on) {
-        // the second pass's twiddles of this tile's blocks: for each stage m
-        // of that pass one contiguous run tw[m (N1 + t0) .. + m n_sub), at
-        // shared offset (m - m0) n_sub, behind the tile
-        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(sm + (size_t)n_sub * (n + n / 16));
-        int off = 0;
-        for (int m = BlockTwStage<LOGN, FWD, COLS>::m0; m < n; m <<= 1) {
-            const int len = m << lsub;
-            const ulonglong2 *src = tw + (i64)m * (P.N1 + t0);
-            for (int j = threadIdx.x; j < len; j += blockDim.x) {
-                const unsigned d = (unsigned)__cvta_generic_to_shared(dst + off + j);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + j) : "memory");
-            }
-            off += len;
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        tws = dst;
-    }
-    run_passes<LOGN, FWD, COLS, LM, SM, Q1, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2, tws);
+    run_passes<LOGN, FWD, COLS, LM, SM, Q1, 0>(sm, lay, tw, tw_b0, tw_bmul, q, lc, sc, t0, P.log_n2);
     if (!gout) {
         // shared -> global with the fused store (coalesced)
         if constexpr (CKKS_NTT_STORE_BATCH && (SM == ST_MRS || SM == ST_ADDSUB)) {
