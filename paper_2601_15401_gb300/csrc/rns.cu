@@ -19,6 +19,12 @@ namespace ckks {
 
 static constexpr int kThreads = 256;
 
+// 1: the tensor kernels for the largest tuples (three children at a k >= 9
+// root) load the next child's terms while multiplying by the current one
+#ifndef CKKS_TENSOR_PREFETCH
+#define CKKS_TENSOR_PREFETCH 1
+#endif
+
 // V adjacent words at p (16-byte loads / stores for even V; p 16-byte aligned)
 template <int V>
 __device__ __forceinline__ void load_span(const u64 *p, u64 (&o)[V]) {
@@ -94,17 +100,30 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
                 for (int e = 0; e < V; ++e) cur[a][e] = 0ull;
         }
     }
-    for (int c = 1; c < v.m(); ++c) {
+    // the largest tuples (three children at a k >= 9 root) load the next
+    // child while multiplying by this one
+    constexpr bool PF = CKKS_TENSOR_PREFETCH && MAXT > 9;
+    auto load_child = [&](int c, u64 (&y)[MAXT][V]) {
         const int ny = v.polys(c);
         const u64 *src = v.src(c) + r;
         const i64 ps = v.pstride(c);
-        u64 y[MAXT][V];
 #pragma unroll
         for (int a = 0; a < MAXT; ++a) {
             if (a < ny) load_span<V>(src + (i64)a * ps, y[a]);
             else
 #pragma unroll
                 for (int e = 0; e < V; ++e) y[a][e] = 0ull;
+        }
+    };
+    u64 y[MAXT][V];
+    if (PF && v.m() > 1) load_child(1, y);
+    for (int c = 1; c < v.m(); ++c) {
+        const int ny = v.polys(c);
+        u64 yn[PF ? MAXT : 1][V];
+        if constexpr (PF) {
+            if (c + 1 < v.m()) load_child(c + 1, yn);
+        } else {
+            load_child(c, y);
         }
         u64 nxt[MAXT][V];
 #pragma unroll
@@ -159,6 +178,12 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
         for (int t = 0; t < MAXT; ++t)
 #pragma unroll
             for (int e = 0; e < V; ++e) cur[t][e] = nxt[t][e];
+        if constexpr (PF) {
+#pragma unroll
+            for (int a = 0; a < MAXT; ++a)
+#pragma unroll
+                for (int e = 0; e < V; ++e) y[a][e] = yn[a][e];
+        }
     }
     const u64 fix = rpow[(i64)j * 16 + v.m()];  // R^m
     u64 *dst = v.dst() + r;
