@@ -129,7 +129,8 @@ int context_build(Context &C, const uint32_t log_n, const uint32_t L, const uint
     std::vector<ModQ> mods(NP);
     std::vector<ulonglong2> twf((size_t)NP * N), twi((size_t)NP * N);
     std::vector<Shoup> ninv(NP), one(NP);
-    std::vector<u64> r2(NP), rpow((size_t)NP * 16), keyfold(NP);
+    std::vector<u64> r2(NP), keyfold(NP);
+    std::vector<Shoup> rfix((size_t)NP * 16);
     std::vector<u64> cK((size_t)NP * CKKS_MAX_PRIMES, 0);
     std::vector<Shoup> invq((size_t)CKKS_MAX_PRIMES * CKKS_MAX_PRIMES);
     std::vector<Shoup> pscale(C.K);
@@ -161,9 +162,12 @@ int context_build(Context &C, const uint32_t log_n, const uint32_t L, const uint
         one[x] = h_shoup(1, m);
         const u64 R = h_R(m);
         r2[x] = h_mul(R, R, m);
+        // rfix[e] = R^(e-1) mod q as a Shoup constant (e >= 1): the factor a
+        // product of e tuples (e - 1 Montgomery products) is short of
+        rfix[(size_t)x * 16] = h_shoup(1 % m, m);
         u64 acc = 1 % m;
-        for (int e = 0; e < 16; ++e) {
-            rpow[(size_t)x * 16 + e] = acc;
+        for (int e = 1; e < 16; ++e) {
+            rfix[(size_t)x * 16 + e] = h_shoup(acc, m);
             acc = h_mul(acc, R, m);
         }
         u64 Pm = 1 % m;
@@ -253,7 +257,7 @@ int context_build(Context &C, const uint32_t log_n, const uint32_t L, const uint
         {pscale.data(), pscale.size() * sizeof(Shoup), (void **)&C.d_pscale},
         {cK.data(), cK.size() * sizeof(u64), (void **)&C.d_cK},
         {r2.data(), r2.size() * sizeof(u64), (void **)&C.d_r2},
-        {rpow.data(), rpow.size() * sizeof(u64), (void **)&C.d_rpow},
+        {rfix.data(), rfix.size() * sizeof(Shoup), (void **)&C.d_rfix},
         {keyfold.data(), keyfold.size() * sizeof(u64), (void **)&C.d_keyfold},
         {invq.data(), invq.size() * sizeof(Shoup), (void **)&C.d_invq},
         {bpre.data(), bpre.size() * sizeof(Shoup), (void **)&C.d_bconv_pre},

@@ -467,7 +467,7 @@ int run_mul_k(const Context &C, const Plan &P, int level, int B, const LimbView 
         T.N = N;
         T.m = (int)nd.children.size();
         T.mods = C.d_mods;
-        T.rpow = C.d_rpow;
+        T.rfix = C.d_rfix;
         for (int c = 0; c < T.m; ++c) {
             int ch = nd.children[c];
             T.child[c] = ch >= 0 ? node_out[ch] : in[-1 - ch];
@@ -648,7 +648,7 @@ int run_mul2(const Context &C, int level, int B, LimbView a, LimbView b, LimbVie
         T.N = N;
         T.m = 2;
         T.mods = C.d_mods;
-        T.rpow = C.d_rpow;
+        T.rfix = C.d_rfix;
         T.child[0] = a;
         T.child[1] = b;
         T.child_polys[0] = T.child_polys[1] = 2;
@@ -711,7 +711,7 @@ cudaError_t run_tensor(const Context &C, int B, int level, int m, const LimbView
     T.N = C.N;
     T.m = m;
     T.mods = C.d_mods;
-    T.rpow = C.d_rpow;
+    T.rfix = C.d_rfix;
     for (int c = 0; c < m; ++c) {
         T.child[c] = in[c];
         T.child_polys[c] = polys[c];

@@ -125,7 +125,7 @@ struct Context {
     Shoup *d_pscale = nullptr;        // [K]     N^-1 [phat_i^-1]_{p_i}
     u64 *d_cK = nullptr;              // [L+K][64]: row j < L: [p_i^-1 R]_{q_j}
     u64 *d_r2 = nullptr;              // [L+K]   R^2 mod q
-    u64 *d_rpow = nullptr;            // [L+K][16] R^e mod q
+    Shoup *d_rfix = nullptr;          // [L+K][16] R^(e-1) mod q (Shoup), e >= 1
     u64 *d_keyfold = nullptr;         // [L+K]   Q limbs: P^-1 R^2, P limbs: R^2 (mod prime)
     Shoup *d_invq = nullptr;          // [64][64] inv(prime i) mod prime j
     Shoup *d_bconv_pre = nullptr;     // [L+1][L] level, limb: N^-1 [(Q_beta/q_j)^-1]_{q_j}

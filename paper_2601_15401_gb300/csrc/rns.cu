@@ -85,7 +85,7 @@ struct TensorTableView {
 // r = limb * N + coefficient (the first of V adjacent ones), j = the limb's
 // prime.
 template <int MAXT, bool Q1, int V, class View>
-__device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const ModQ m, const u64 *rpow) {
+__device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const ModQ m, const Shoup *rfix) {
     const u64 q = m.q;
     u64 cur[MAXT][V];
     int ncur = v.polys(0);
@@ -185,7 +185,10 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
                 for (int e = 0; e < V; ++e) y[a][e] = yn[a][e];
         }
     }
-    const u64 fix = rpow[(i64)j * 16 + v.m()];  // R^m
+    // m children took m - 1 Montgomery products: multiply by R^(m-1) (a
+    // Shoup product by a constant; the Montgomery product by R^m it replaces
+    // cost a 128-bit product and a REDC)
+    const Shoup fix = rfix[(i64)j * 16 + v.m()];
     u64 *dst = v.dst() + r;
     const i64 ds = v.dstride();
 #pragma unroll
@@ -193,7 +196,7 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
         if (t < ncur) {
             u64 o[V];
 #pragma unroll
-            for (int e = 0; e < V; ++e) o[e] = mont_mul_t<Q1>(cur[t][e], fix, m);
+            for (int e = 0; e < V; ++e) o[e] = shoup_t<Q1>(cur[t][e], fix.w, fix.wp, m.q);
             store_span<V>(dst + (i64)t * ds, o);
         }
 }
@@ -210,14 +213,14 @@ __global__ void __launch_bounds__(kThreads, TensorOcc<MAXT>::minb) tensor_kernel
     const i64 r = ((i64)blockIdx.x * blockDim.x + threadIdx.x) * V;  // limb * N + coefficient
     if (r >= (i64)A.level * A.N) return;
     const int j = (int)(r >> A.log_n);
-    tensor_coeff<MAXT, Q1, V>(TensorUniformView{A, (int)blockIdx.y}, r, j, A.mods[j], A.rpow);
+    tensor_coeff<MAXT, Q1, V>(TensorUniformView{A, (int)blockIdx.y}, r, j, A.mods[j], A.rfix);
 }
 
 // Table launch: blockIdx.y = tree node; the node's entry is staged in shared
 // memory (it is indexed by child at run time).
 template <int MAXT, bool Q1, int V>
 __global__ void __launch_bounds__(kThreads, TensorOcc<MAXT>::minb) tensor_table_kernel(const TensorJob *jobs, int N, int log_n,
-                                                                const ModQ *mods, const u64 *rpow) {
+                                                                const ModQ *mods, const Shoup *rfix) {
     __shared__ TensorJob J;
     {
         // the entry is copied by many threads, one word each
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, TensorOcc<MAXT>::minb) tensor_table_
     const i64 r = ((i64)blockIdx.x * blockDim.x + threadIdx.x) * V;
     if (r >= (i64)J.level * N) return;
     const int j = (int)(r >> log_n);
-    tensor_coeff<MAXT, Q1, V>(TensorTableView{J}, r, j, mods[j], rpow);
+    tensor_coeff<MAXT, Q1, V>(TensorTableView{J}, r, j, mods[j], rfix);
 }
 
 // 64 x 64 -> 128-bit products per coefficient of a node's tensor product
@@ -247,7 +250,7 @@ double tensor_products_per_coeff(const int *polys, int m) {
         ncur += ny - 1;
         ops += ncur;  // REDC of every term
     }
-    return ops + ncur;  // the final R^m correction
+    return ops + ncur;  // the final R^(m-1) correction (a Shoup product)
 }
 
 // Tuples of up to 5 terms take two adjacent coefficients per thread
@@ -273,7 +276,7 @@ static void launch_tensor_sized(int maxt, dim3 blocks, const TensorArgs &A, cuda
 template <bool Q1, int V>
 static void launch_tensor_table_sized(const Context &C, int maxt, dim3 blocks, const TensorJob *jobs,
                                       cudaStream_t st) {
-#define CKKS_TT(MT, VV) tensor_table_kernel<MT, Q1, VV><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rpow)
+#define CKKS_TT(MT, VV) tensor_table_kernel<MT, Q1, VV><<<blocks, kThreads, 0, st>>>(jobs, C.N, C.log_n, C.d_mods, C.d_rfix)
     if (maxt <= 3) CKKS_TT(3, V);
     else if (maxt <= 4) CKKS_TT(4, V);
     else if (maxt <= 5 && (V == 1 || kTensorVecMaxT >= 5)) CKKS_TT(5, V);

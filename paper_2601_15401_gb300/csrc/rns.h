@@ -14,7 +14,7 @@ struct TensorArgs {
     int child_polys[CKKS_MAX_CHILDREN];
     LimbView out;
     const ModQ *mods;
-    const u64 *rpow;                     // [prime][16] R^e
+    const Shoup *rfix;                   // [prime][16] R^(e-1) mod prime (Shoup constants)
 };
 
 struct BconvArgs {
