@@ -503,7 +503,13 @@ int ckks_peak_int(int kind, uint64_t q, const uint64_t *w, const uint64_t *wp, i
  * Shoup quotient product and Montgomery's q^-1 and quotient products with
  * 32-bit multiplies (q = h 2^32 + 1); 0 keeps the general 64-bit forms.
  * Residues are the same either way; for other primes the value has no
- * effect. */
+ * effect.
+ * Tensor product kernels (Eq. 13): "tensor_fixed" 1 (default) runs the
+ * product of a tree node whose two or three children are all tuples of at
+ * least four terms, in one of the compiled shapes (two children of 4..7
+ * terms; three of 4 or 5), through a kernel unrolled for exactly that
+ * shape; 0 sends every node to the kernels bounded by the largest tuple
+ * size. Residues are the same either way. */
 int ckks_tune_set(ckks_context *ctx, const char *key, int value);
 int ckks_tune_get(const ckks_context *ctx, const char *key, int *value);
 

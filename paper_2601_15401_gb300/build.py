@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.environ.get("CKKS_MULK_LIB", os.path.join(HERE, "libckks_mulk.so"))
 SOURCES = ["ntt.cu", "ntt_uf.cu", "ntt_ui.cu", "ntt_tf.cu", "ntt_ti.cu", "ntt_uf1.cu", "ntt_ui1.cu", "ntt_tf1.cu",
-           "ntt_ti1.cu", "rns.cu", "context.cu", "engine.cu", "capi.cu", "plan.cpp", "noalloc.cu", "encrypt.cu", "galois.cu", "embed.cu", "check.cu", "peak.cu", "wave.cu", "xfer.cu"]
+           "ntt_ti1.cu", "rns.cu", "tensor_fixed.cu", "context.cu", "engine.cu", "capi.cu", "plan.cpp", "noalloc.cu", "encrypt.cu", "galois.cu", "embed.cu", "check.cu", "peak.cu", "wave.cu", "xfer.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

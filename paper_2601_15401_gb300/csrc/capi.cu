@@ -721,6 +721,7 @@ static int *tune_slot(ckks_context *ctx, const char *key, int &lo, int &hi) {
     if (!strcmp(key, "check_residues")) { lo = 0; hi = 1; return &ctx->c.tune_check_residues; }
     if (!strcmp(key, "nvtx")) { lo = 0; hi = 1; return &ctx->c.tune_nvtx; }
     if (!strcmp(key, "q1_forms")) { lo = 0; hi = 1; return &ctx->c.tune_q1; }
+    if (!strcmp(key, "tensor_fixed")) { lo = 0; hi = 1; return &ctx->c.tune_tensor_fixed; }
     return nullptr;
 }
 

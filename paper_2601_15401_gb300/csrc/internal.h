@@ -155,6 +155,10 @@ struct Context {
     // CKKS_ECHECK on a violation); 1 = NVTX ranges per tree node and stage
     int tune_check_residues = 0;
     int tune_nvtx = 0;
+    // tensor products of tree nodes whose children are all multi-term tuples
+    // and whose shape is one of the compiled ones (rns.cu, kFixedShapes) run
+    // exactly unrolled kernels for that shape; 0 = the bounded generic kernels
+    int tune_tensor_fixed = 1;
     // every prime (Q and P) is 1 (mod 2^32): the kernels can then take the
     // cheaper forms of the Shoup product and of REDC (shoup_lazy_q1,
     // redc_q1); set at creation. tune_q1 = 0 keeps the general forms.

@@ -57,29 +57,6 @@ __device__ __forceinline__ void store_span(u64 *p, const u64 (&v)[V]) {
 // wise in the NTT domain. Each child product is a Montgomery product, so the
 // result carries R^-(m-1); the final multiply by R^m (REDC) removes it.
 // ---------------------------------------------------------------------------
-// Where a tensor-product CTA finds its children and output: the uniform
-// batch of a launch (TensorArgs, batch element b) or one table entry.
-struct TensorUniformView {
-    const TensorArgs &A;
-    int b;
-    __device__ __forceinline__ int m() const { return A.m; }
-    __device__ __forceinline__ int polys(int c) const { return A.child_polys[c]; }
-    __device__ __forceinline__ const u64 *src(int c) const { return A.child[c].ptr + (i64)b * A.child[c].bstride; }
-    __device__ __forceinline__ i64 pstride(int c) const { return A.child[c].pstride; }
-    __device__ __forceinline__ u64 *dst() const { return A.out.ptr + (i64)b * A.out.bstride; }
-    __device__ __forceinline__ i64 dstride() const { return A.out.pstride; }
-};
-
-struct TensorTableView {
-    const TensorJob &J;
-    __device__ __forceinline__ int m() const { return J.m; }
-    __device__ __forceinline__ int polys(int c) const { return J.cpolys[c]; }
-    __device__ __forceinline__ const u64 *src(int c) const { return J.child[c]; }
-    __device__ __forceinline__ i64 pstride(int c) const { return J.cstride[c]; }
-    __device__ __forceinline__ u64 *dst() const { return J.out; }
-    __device__ __forceinline__ i64 dstride() const { return J.ostride; }
-};
-
 // MAXT bounds every tuple size involved (children and output), so the
 // unrolled, predicated product loops stay short for small nodes.
 // r = limb * N + coefficient (the first of V adjacent ones), j = the limb's
@@ -296,6 +273,13 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t 
     TensorArgs A = Ain;
     A.log_n = C.log_n;
     count_kernel(C);
+    // a node shape with a fixed kernel: children sorted by size
+    int code = -1;
+    if (C.tune_tensor_fixed) {
+        TensorArgs S = A;
+        code = tensor_sort_children(S);
+        if (code >= 0) A = S;
+    }
     int in_polys = 0, maxt = 0;
     bool vec2 = view_vec2(A.out);
     for (int c = 0; c < A.m; ++c) {
@@ -309,6 +293,7 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t 
     const double coeffs = (double)A.n_batch * A.level * A.N;
     ProfScope ps(C, KC_TENSOR, (double)(in_polys + out_polys) * coeffs * sizeof(u64), st,
                  coeffs * tensor_products_per_coeff(A.child_polys, A.m));
+    if (code >= 0) return launch_tensor_fixed(C, A, code, st);
     const i64 per = vec2 ? 2 * kThreads : kThreads;
     dim3 blocks((unsigned)(((i64)A.level * A.N + per - 1) / per), A.n_batch);
     if (vec2) {

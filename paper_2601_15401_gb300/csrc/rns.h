@@ -96,13 +96,57 @@ struct MacTarget {                       // accumulator limb x of product `job` 
     int job, x, job2, pad;               // shape, when the target pairs two products; else job2 = -1)
 };
 
+// Where a tensor-product CTA finds its children and output: the uniform
+// batch of a launch (TensorArgs, batch element b) or one table entry.
+struct TensorUniformView {
+    const TensorArgs &A;
+    int b;
+    __device__ __forceinline__ int m() const { return A.m; }
+    __device__ __forceinline__ int polys(int c) const { return A.child_polys[c]; }
+    __device__ __forceinline__ const u64 *src(int c) const { return A.child[c].ptr + (i64)b * A.child[c].bstride; }
+    __device__ __forceinline__ i64 pstride(int c) const { return A.child[c].pstride; }
+    __device__ __forceinline__ u64 *dst() const { return A.out.ptr + (i64)b * A.out.bstride; }
+    __device__ __forceinline__ i64 dstride() const { return A.out.pstride; }
+};
+
+struct TensorTableView {
+    const TensorJob &J;
+    __device__ __forceinline__ int m() const { return J.m; }
+    __device__ __forceinline__ int polys(int c) const { return J.cpolys[c]; }
+    __device__ __forceinline__ const u64 *src(int c) const { return J.child[c]; }
+    __device__ __forceinline__ i64 pstride(int c) const { return J.cstride[c]; }
+    __device__ __forceinline__ u64 *dst() const { return J.out; }
+    __device__ __forceinline__ i64 dstride() const { return J.ostride; }
+};
+
 cudaError_t launch_tensor(const Context &C, const TensorArgs &A, cudaStream_t st);
+// Node shapes with exactly unrolled tensor kernels (children sorted by
+// tuple size, largest first; c = 0 for two children): two children of 4..7
+// terms (codes 0..9) except 6 and 4 (children of 5 and 3 inputs: no tree
+// within the depth rule has that node for k <= 16), three of 4 or 5 terms
+// (codes 10..13); -1 otherwise.
+__host__ __device__ inline int tensor_fixed_code(int m, int a, int b, int c) {
+    if (m == 2 && b >= 4 && b <= a && a <= 7 && !(a == 6 && b == 4)) return (a - 4) * (a - 3) / 2 + (b - 4);
+    if (m == 3 && c >= 4 && c <= b && b <= a && a <= 5) return 10 + (a - 4) + (b - 4) + (c - 4);
+    return -1;
+}
+// The node's children sorted by tuple size, largest first (the product is
+// commutative, so the order does not change the result); the shape code of
+// the sorted node, -1 when no fixed kernel covers it.
+int tensor_sort_children(TensorJob &T);
+int tensor_sort_children(TensorArgs &A);
+// Uniform launch of a node of shape `code` (children sorted); the caller
+// counts and times it.
+cudaError_t launch_tensor_fixed(const Context &C, const TensorArgs &A, int code, cudaStream_t st);
 // vec2: every entry's pointers are 16-byte aligned and its strides even
 // (tensor_job_vec2), so tuples of up to 5 terms may take two coefficients
 // per thread
 bool tensor_job_vec2(const TensorJob &T);
 cudaError_t launch_tensor_table(const Context &C, const TensorJob *jobs, int n_jobs, int maxt, int max_level,
                                 bool vec2, double bytes, double ops, cudaStream_t st);
+// Table launch of nodes that all have the (sorted) shape `code`.
+cudaError_t launch_tensor_fixed_table(const Context &C, const TensorJob *jobs, int n_jobs, int code, int max_level,
+                                      double bytes, double ops, cudaStream_t st);
 double tensor_products_per_coeff(const int *polys, int m);
 cudaError_t launch_rschain_table(const Context &C, const RsJob *jobs, int n_jobs, int max_polys, double bytes,
                                  cudaStream_t st);

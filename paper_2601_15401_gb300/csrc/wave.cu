@@ -14,7 +14,8 @@
 // of a group (tensor, INTT, rescale chain, NTT, BConv, MAC, ...) is one
 // launch over all products whose tree has work there. A batch of any mix of
 // k and levels therefore takes a fixed number of launches:
-// heights x 6 + 14 (+ one tensor launch per tuple-size class).
+// heights x 6 + 14 (+ one tensor launch per tuple-size class, and one per
+// node shape with a fixed kernel, tensor_fixed.cu).
 //
 // Memory: two caller buffers, the job tables (written on the first run with
 // that pair of buffers, by one host-to-device copy on the run's stream) and
@@ -61,6 +62,12 @@ struct Stage {
     StoreSpec S{};
     int maxt = 0, max_level = 0, max_polys = 0;
     bool vec2 = true;  // tensor: every entry 16-byte aligned with even strides
+    bool fixed = false;  // tensor: every entry has a fixed-shape kernel
+    struct FixedRun {    // tensor, fixed: entries [first, first + count) have shape `code`
+        int code, first, count, max_level;
+        double bytes, ops;
+    };
+    std::vector<FixedRun> runs;
     int n_pairs = 0;   // key MAC: targets[0 .. n_pairs) pair two products
     std::vector<NttJob> ntt;
     std::vector<TensorJob> tensor;
@@ -215,10 +222,19 @@ void build_product(Builder &B, const WaveProduct &w, Bump &ws) {
         T.out = d;
         T.ostride = dps;
         const int round = nd.root ? B.H : height[i] - 1;
-        // tuple-size class of the tensor launch (its instantiation)
-        const int cls = maxt <= 3 ? 0 : maxt <= 4 ? 1 : maxt <= 5 ? 2 : maxt <= 7 ? 3 : maxt <= 9 ? 4 : 5;
+        // tuple-size class of the tensor launch (its instantiation); class 6:
+        // shapes with fixed kernels (children sorted by size)
+        int cls = maxt <= 3 ? 0 : maxt <= 4 ? 1 : maxt <= 5 ? 2 : maxt <= 7 ? 3 : maxt <= 9 ? 4 : 5;
+        if (C.tune_tensor_fixed) {
+            TensorJob S = T;
+            if (tensor_sort_children(S) >= 0) {
+                T = S;
+                cls = 6;
+            }
+        }
         if (emit) {
             Stage &s = B.at(round, cls, SK_TENSOR);
+            s.fixed = cls == 6;
             s.tensor.push_back(T);
             s.vec2 = s.vec2 && tensor_job_vec2(T);
             s.maxt = std::max(s.maxt, maxt);
@@ -448,6 +464,29 @@ int build(ckks_wave &W, char *scratch, std::vector<char> &tables) {
         Stage &s = kv.second;
         if (s.count() == 0) continue;
         if (s.kind == SK_NTT) s.off = put(tables, s.ntt);
+        if (s.kind == SK_TENSOR && s.fixed) {
+            // one launch per shape: entries grouped by shape code
+            // (the entries' children were sorted when they were built)
+            auto code_of = [](const TensorJob &T) {
+                return tensor_fixed_code(T.m, T.cpolys[0], T.cpolys[1], T.m > 2 ? T.cpolys[2] : 0);
+            };
+            std::stable_sort(s.tensor.begin(), s.tensor.end(),
+                             [&](const TensorJob &a, const TensorJob &b) { return code_of(a) < code_of(b); });
+            s.runs.clear();
+            const double limb = (double)C.N * sizeof(u64);
+            for (int i = 0; i < (int)s.tensor.size(); ++i) {
+                const TensorJob &T = s.tensor[i];
+                const int code = code_of(T);
+                if (s.runs.empty() || s.runs.back().code != code) s.runs.push_back({code, i, 0, 0, 0.0, 0.0});
+                Stage::FixedRun &r = s.runs.back();
+                int in_polys = 0;
+                for (int c = 0; c < T.m; ++c) in_polys += T.cpolys[c];
+                r.count += 1;
+                r.max_level = std::max(r.max_level, T.level);
+                r.bytes += (double)(2 * in_polys - T.m + 1) * T.level * limb;
+                r.ops += (double)T.level * C.N * tensor_products_per_coeff(T.cpolys, T.m);
+            }
+        }
         if (s.kind == SK_TENSOR) s.off = put(tables, s.tensor);
         if (s.kind == SK_RSCHAIN) s.off = put(tables, s.rs);
         if (s.kind == SK_BCONV) s.off = put(tables, s.bconv);
@@ -505,8 +544,15 @@ cudaError_t enqueue(ckks_wave &W, char *ws /* the job tables */, cudaStream_t st
                                        st);
             break;
         case SK_TENSOR:
-            e = launch_tensor_table(C, (const TensorJob *)(ws + s.off), n, s.maxt, s.max_level, s.vec2, s.bytes, s.ops,
-                                    st);
+            if (s.fixed) {
+                for (const Stage::FixedRun &r : s.runs) {
+                    e = launch_tensor_fixed_table(C, (const TensorJob *)(ws + s.off) + r.first, r.count, r.code,
+                                                  r.max_level, r.bytes, r.ops, st);
+                    if (e != cudaSuccess) break;
+                }
+            } else
+                e = launch_tensor_table(C, (const TensorJob *)(ws + s.off), n, s.maxt, s.max_level, s.vec2, s.bytes,
+                                        s.ops, st);
             break;
         case SK_RSCHAIN:
             e = launch_rschain_table(C, (const RsJob *)(ws + s.off), n, s.max_polys, s.bytes, st);
