@@ -25,6 +25,13 @@ static constexpr int kThreads = 256;
 #define CKKS_TENSOR_PREFETCH 1
 #endif
 
+// 1: the R^(m-1) correction of a node's m - 1 Montgomery products is applied
+// to the terms of its last child (the smallest: the host sorts children by
+// size) before they are multiplied, instead of to every output term
+#ifndef CKKS_TENSOR_PRESCALE
+#define CKKS_TENSOR_PRESCALE 1
+#endif
+
 // V adjacent words at p (16-byte loads / stores for even V; p 16-byte aligned)
 template <int V>
 __device__ __forceinline__ void load_span(const u64 *p, u64 (&o)[V]) {
@@ -55,7 +62,8 @@ __device__ __forceinline__ void store_span(u64 *p, const u64 (&v)[V]) {
 // ---------------------------------------------------------------------------
 // tensor product: out = prod over children of (sum_l c_l s^l), coefficient-
 // wise in the NTT domain. Each child product is a Montgomery product, so the
-// result carries R^-(m-1); the final multiply by R^m (REDC) removes it.
+// m - 1 products leave R^-(m-1); the smallest child's terms are multiplied
+// by R^(m-1) before they enter (a Shoup product by a per-prime constant).
 // ---------------------------------------------------------------------------
 // MAXT bounds every tuple size involved (children and output), so the
 // unrolled, predicated product loops stay short for small nodes.
@@ -92,6 +100,10 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
                 for (int e = 0; e < V; ++e) y[a][e] = 0ull;
         }
     };
+    // m children take m - 1 Montgomery products, which leave R^-(m-1): the
+    // terms of the last child are multiplied by R^(m-1) first (a Shoup
+    // product by a per-prime constant), or else every output term after
+    const Shoup fix = rfix[(i64)j * 16 + v.m()];
     u64 y[MAXT][V];
     if (PF && v.m() > 1) load_child(1, y);
     for (int c = 1; c < v.m(); ++c) {
@@ -101,6 +113,13 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
             if (c + 1 < v.m()) load_child(c + 1, yn);
         } else {
             load_child(c, y);
+        }
+        if (CKKS_TENSOR_PRESCALE && c == v.m() - 1) {
+#pragma unroll
+            for (int a = 0; a < MAXT; ++a)
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (a < ny) y[a][e] = shoup_t<Q1>(y[a][e], fix.w, fix.wp, q);
         }
         u64 nxt[MAXT][V];
 #pragma unroll
@@ -162,10 +181,6 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
                 for (int e = 0; e < V; ++e) y[a][e] = yn[a][e];
         }
     }
-    // m children took m - 1 Montgomery products: multiply by R^(m-1) (a
-    // Shoup product by a constant; the Montgomery product by R^m it replaces
-    // cost a 128-bit product and a REDC)
-    const Shoup fix = rfix[(i64)j * 16 + v.m()];
     u64 *dst = v.dst() + r;
     const i64 ds = v.dstride();
 #pragma unroll
@@ -173,7 +188,8 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
         if (t < ncur) {
             u64 o[V];
 #pragma unroll
-            for (int e = 0; e < V; ++e) o[e] = shoup_t<Q1>(cur[t][e], fix.w, fix.wp, m.q);
+            for (int e = 0; e < V; ++e)
+                o[e] = CKKS_TENSOR_PRESCALE ? cur[t][e] : shoup_t<Q1>(cur[t][e], fix.w, fix.wp, m.q);
             store_span<V>(dst + (i64)t * ds, o);
         }
 }
@@ -227,7 +243,12 @@ double tensor_products_per_coeff(const int *polys, int m) {
         ncur += ny - 1;
         ops += ncur;  // REDC of every term
     }
-    return ops + ncur;  // the final R^(m-1) correction (a Shoup product)
+    // the R^(m-1) correction (Shoup products): on the smallest child's terms
+    // (children sorted by size, CKKS_TENSOR_PRESCALE) or on the output's
+    int corr = ncur;
+    if (CKKS_TENSOR_PRESCALE)
+        for (int c = 0; c < m; ++c) corr = std::min(corr, polys[c]);
+    return ops + corr;
 }
 
 // Tuples of up to 5 terms take two adjacent coefficients per thread
@@ -273,13 +294,10 @@ cudaError_t launch_tensor(const Context &C, const TensorArgs &Ain, cudaStream_t 
     TensorArgs A = Ain;
     A.log_n = C.log_n;
     count_kernel(C);
-    // a node shape with a fixed kernel: children sorted by size
-    int code = -1;
-    if (C.tune_tensor_fixed) {
-        TensorArgs S = A;
-        code = tensor_sort_children(S);
-        if (code >= 0) A = S;
-    }
+    // children sorted by size, largest first (the smallest, last, takes the
+    // R^(m-1) correction); a node shape with a fixed kernel takes it
+    int code = tensor_sort_children(A);
+    if (!C.tune_tensor_fixed) code = -1;
     int in_polys = 0, maxt = 0;
     bool vec2 = view_vec2(A.out);
     for (int c = 0; c < A.m; ++c) {

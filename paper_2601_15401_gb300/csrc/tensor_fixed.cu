@@ -20,6 +20,10 @@
 #include "internal.h"
 #include "rns.h"
 
+#ifndef CKKS_TENSOR_PRESCALE
+#define CKKS_TENSOR_PRESCALE 1
+#endif
+
 namespace ckks {
 
 namespace {
@@ -41,8 +45,8 @@ __device__ __forceinline__ void conv_redc(const u64 (&x)[A], const u64 (&y)[B], 
     }
 }
 
-// the same, each term multiplied by the Shoup constant fix and stored at
-// dst + t ds as soon as it is formed
+// the same, each term stored at dst + t ds as soon as it is formed (with
+// CKKS_TENSOR_PRESCALE = 0 multiplied by the Shoup constant fix first)
 template <int A, int B, bool Q1>
 __device__ __forceinline__ void conv_redc_store(const u64 (&x)[A], const u64 (&y)[B], const ModQ m, const Shoup fix,
                                                 u64 *dst, i64 ds) {
@@ -54,7 +58,8 @@ __device__ __forceinline__ void conv_redc_store(const u64 (&x)[A], const u64 (&y
 #pragma unroll
         for (int b = 0; b < B; ++b)
             if (t - b >= 0 && t - b < A) acc.mac(x[t - b], y[b]);
-        dst[(i64)t * ds] = shoup_t<Q1>(redc_t<Q1>(acc.hi, acc.lo, m), fix.w, fix.wp, m.q);
+        const u64 z = redc_t<Q1>(acc.hi, acc.lo, m);
+        dst[(i64)t * ds] = CKKS_TENSOR_PRESCALE ? z : shoup_t<Q1>(z, fix.w, fix.wp, m.q);
     }
 }
 
@@ -64,9 +69,18 @@ __device__ __forceinline__ void load_terms(const u64 *src, i64 ps, u64 (&o)[T]) 
     for (int a = 0; a < T; ++a) o[a] = src[(i64)a * ps];
 }
 
+// the terms of the last (smallest) child times R^(m-1)
+template <int T, bool Q1>
+__device__ __forceinline__ void prescale(u64 (&o)[T], const Shoup fix, u64 q) {
+    if (CKKS_TENSOR_PRESCALE)
+#pragma unroll
+        for (int a = 0; a < T; ++a) o[a] = shoup_t<Q1>(o[a], fix.w, fix.wp, q);
+}
+
 // One coefficient r (= limb j * N + coefficient) of a node with children of
-// A, B (and C; 0 for two children) terms: m - 1 Montgomery products, then
-// R^(m-1) as a Shoup product by the per-prime constant rfix[j][m].
+// A, B (and C; 0 for two children) terms: m - 1 Montgomery products, which
+// leave R^-(m-1), and R^(m-1) as a Shoup product by the per-prime constant
+// rfix[j][m] on the terms of the last child.
 template <int A, int B, int C, bool Q1, class View>
 __device__ __forceinline__ void tensor_fixed_coeff(const View &v, i64 r, int j, const ModQ m, const Shoup *rfix) {
     u64 x[A], y[B];
@@ -75,13 +89,17 @@ __device__ __forceinline__ void tensor_fixed_coeff(const View &v, i64 r, int j, 
     u64 *dst = v.dst() + r;
     const i64 ds = v.dstride();
     if constexpr (C == 0) {
-        conv_redc_store<A, B, Q1>(x, y, m, rfix[(i64)j * 16 + 2], dst, ds);
+        const Shoup fix = rfix[(i64)j * 16 + 2];
+        prescale<B, Q1>(y, fix, m.q);
+        conv_redc_store<A, B, Q1>(x, y, m, fix, dst, ds);
     } else {
+        const Shoup fix = rfix[(i64)j * 16 + 3];
         u64 w[C];
         load_terms<C>(v.src(2) + r, v.pstride(2), w);
         u64 z[A + B - 1];
         conv_redc<A, B, Q1>(x, y, z, m);
-        conv_redc_store<A + B - 1, C, Q1>(z, w, m, rfix[(i64)j * 16 + 3], dst, ds);
+        prescale<C, Q1>(w, fix, m.q);
+        conv_redc_store<A + B - 1, C, Q1>(z, w, m, fix, dst, ds);
     }
 }
 

@@ -225,13 +225,9 @@ void build_product(Builder &B, const WaveProduct &w, Bump &ws) {
         // tuple-size class of the tensor launch (its instantiation); class 6:
         // shapes with fixed kernels (children sorted by size)
         int cls = maxt <= 3 ? 0 : maxt <= 4 ? 1 : maxt <= 5 ? 2 : maxt <= 7 ? 3 : maxt <= 9 ? 4 : 5;
-        if (C.tune_tensor_fixed) {
-            TensorJob S = T;
-            if (tensor_sort_children(S) >= 0) {
-                T = S;
-                cls = 6;
-            }
-        }
+        // children sorted by size, largest first (the smallest, last, takes
+        // the R^(m-1) correction)
+        if (tensor_sort_children(T) >= 0 && C.tune_tensor_fixed) cls = 6;
         if (emit) {
             Stage &s = B.at(round, cls, SK_TENSOR);
             s.fixed = cls == 6;
