@@ -147,6 +147,14 @@ struct Acc128Lazy {
         lo += plo;
         hi += phi + (lo < plo ? 1ull : 0ull);
     }
+    // add the 128-bit value vhi 2^64 + vlo
+    __device__ __forceinline__ void add(u64 vhi, u64 vlo) {
+        lo += vlo;
+        hi += vhi + (lo < vlo ? 1ull : 0ull);
+    }
+    // the same calls as Acc128 (the modulus is not needed)
+    __device__ __forceinline__ void mac(u64 a, u64 b, u64) { mac(a, b); }
+    __device__ __forceinline__ void add(u64 vhi, u64 vlo, u64) { add(vhi, vlo); }
 };
 
 // Shoup constant pair.

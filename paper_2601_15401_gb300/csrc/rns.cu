@@ -14,6 +14,7 @@
 #include "rns.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace ckks {
 
@@ -31,6 +32,13 @@ static constexpr int kThreads = 256;
 #ifndef CKKS_TENSOR_PRESCALE
 #define CKKS_TENSOR_PRESCALE 1
 #endif
+
+// 1: the bounded kernels' 128-bit sums reduce their high word once, at the
+// REDC (the bounds are stated where the sums are formed); 0: after every term
+#ifndef CKKS_TENSOR_LAZY
+#define CKKS_TENSOR_LAZY 1
+#endif
+using TensorAcc = std::conditional<CKKS_TENSOR_LAZY != 0, Acc128Lazy, Acc128>::type;
 
 // V adjacent words at p (16-byte loads / stores for even V; p 16-byte aligned)
 template <int V>
@@ -129,7 +137,11 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
                 // tuple (Fig. 2(b)): for (c_a, c_{a+1}) the cross term
                 // c_a y1 + c_{a+1} y0 = (c_a + c_{a+1})(y0 + y1) - c_a y0 - c_{a+1} y1,
                 // an exact non-negative integer, so it stays in the 128-bit sums.
-                Acc128 acc[MAXT];
+                // A sum takes p1 of its own pair, the cross term (< 2 q^2) of
+                // the pair below and p2 of the pair below that, or the
+                // unpaired products: below 4 q^2 < q 2^64 (q < 2^61), so its
+                // high word stays below q without a reduction per term.
+                TensorAcc acc[MAXT];
 #pragma unroll
                 for (int t = 0; t < MAXT; ++t) acc[t].zero();
                 const u64 y0 = y[0][e], y1 = y[1][e];
@@ -157,9 +169,12 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
                 for (int t = 0; t < MAXT; ++t)
                     nxt[t][e] = t < ncur + 1 ? redc_t<Q1>(acc[t].hi, acc[t].lo, m) : 0ull;
             } else {
+                // a term sums at most min(ncur, ny) <= 7 products (ncur + ny
+                // - 1 <= 13) of reduced residues: below q 2^64, no reduction
+                // per term
 #pragma unroll
                 for (int t = 0; t < MAXT; ++t) {
-                    Acc128 acc;
+                    TensorAcc acc;
                     acc.zero();
 #pragma unroll
                     for (int a = 0; a <= t; ++a) {
