@@ -209,11 +209,15 @@ __device__ __forceinline__ void tensor_coeff(const View &v, i64 r, int j, const 
         }
 }
 
-// Three CTAs of 256 threads per SM (at most 85 registers) up to 9-term
-// tuples; two for the largest.
+// CTAs of 256 threads per SM: four (at most 64 registers) up to 4-term
+// tuples, whose launches are bound by HBM and need the loads of more
+// threads in flight; three (at most 85) up to 9 terms; two for the largest.
+#ifndef CKKS_TENSOR_SMALL_MINB
+#define CKKS_TENSOR_SMALL_MINB 4
+#endif
 template <int MAXT>
 struct TensorOcc {
-    static constexpr int minb = MAXT <= 9 ? 3 : 2;
+    static constexpr int minb = MAXT <= 4 ? CKKS_TENSOR_SMALL_MINB : MAXT <= 9 ? 3 : 2;
 };
 
 template <int MAXT, bool Q1, int V>
