@@ -817,7 +817,7 @@ def run_reference(args, rank, world):
 KERNEL_SOURCES = {
     "ntt": ["ntt.cu", "ntt_kernel.cuh", "ntt_uf.cu", "ntt_ui.cu", "ntt_tf.cu", "ntt_ti.cu", "ntt_uf1.cu", "ntt_ui1.cu",
             "ntt_tf1.cu", "ntt_ti1.cu", "common.cuh", "internal.h"],
-    "rns": ["rns.cu", "rns.h", "common.cuh", "internal.h"],
+    "rns": ["rns.cu", "tensor_fixed.cu", "rns.h", "common.cuh", "internal.h"],
 }
 
 
