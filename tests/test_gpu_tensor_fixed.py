@@ -14,13 +14,13 @@ import pytest
 
 import synth
 from oracle import ckks as O
-from oracle import plan as OP
 
 from gpu_common import Setup, dev, host, oracle_tuple
 
 pytestmark = pytest.mark.gpu
 
-# k, partition, sorted child tuple sizes of the node with a fixed kernel
+# k, partition, sorted child tuple sizes of the node with a fixed kernel (each
+# a valid tree with that root: tests/test_tensor_shapes_host.py)
 CASES = [
     (6, "(3,3)", (4, 4)),
     (7, "(4,3)|(2,2)", (5, 4)),
@@ -47,13 +47,6 @@ def S():
 
 def _inputs(S, k, seed):
     return [synth.uniform_tuple(S.params, 2, LEVEL, 311, seed + u) for u in range(k)]
-
-
-def test_cases_are_valid_trees_with_the_stated_root_shape():
-    for k, part, shape in CASES:
-        root = OP.parse(part, k)
-        assert OP.valid(root, k), part
-        assert tuple(sorted((c.size + 1 for c in root.children), reverse=True)) == shape, part
 
 
 @pytest.mark.parametrize("fixed", [1, 0])
