@@ -598,7 +598,8 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
         fraction of the link's rate after device compute, and the GPU's loads
         take SM slots from the multiplies, so each carries part; "pull" sends
         every element through the GPU's loads; "auto" (default) keeps the
-        fastest of the mixed split, half-and-half and "pull"."""
+        fastest of six splits, from every element by the copy engines to
+        every element by the GPU's loads."""
         dst = sets[cur_set[0]][0][k][b]
         if b >= B - npull[0]:
             G.pull(dst, host_in[b, :k], blocks=sms * args.pull_ctas_per_sm, stream=cs)
@@ -704,10 +705,10 @@ def e2e_leg(args, ctx, evk, ks, B, L, N, depth, dev, stream, ws, world, dev_inp,
     if args.h2d == "auto":
         # the copy engines' rate next to device compute differs between
         # boxes (94-210 GB/s measured), the GPU's own loads hold ~210 GB/s
-        # but take SM slots: time two untimed steps of each split (a
-        # quarter, half, or all of the batch elements by GPU loads) and keep
-        # the faster
-        for n in sorted({n_mixed, B // 2, B}):
+        # but take SM slots: time two untimed steps of each split (none, an
+        # eighth, a quarter, half, three quarters or all of the batch
+        # elements by GPU loads) and keep the fastest
+        for n in sorted({0, B // 8, n_mixed, B // 2, (3 * B) // 4, B}):
             npull[0] = n
             step()
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -845,7 +846,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--h2d", default="auto", choices=["auto", "mixed", "pull", "copy"],
                     help="e2e uploads: copy engines, GPU loads over the host link (pull), both (mixed), or the "
-                         "fastest of mixed, half-and-half and pull in two untimed steps each (auto)")
+                         "fastest of six splits from all copy engines to all GPU loads in two untimed steps each (auto)")
     ap.add_argument("--pull-fraction", type=float, default=0.25,
                     help="--h2d mixed / auto: share of the batch elements uploaded by GPU loads")
     ap.add_argument("--pull-ctas-per-sm", type=int, default=1, help="64-thread CTAs per SM of the e2e uploads")
