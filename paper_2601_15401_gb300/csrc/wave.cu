@@ -13,9 +13,10 @@
 // height (a node's children always have a smaller height), and each stage
 // of a group (tensor, INTT, rescale chain, NTT, BConv, MAC, ...) is one
 // launch over all products whose tree has work there. A batch of any mix of
-// k and levels therefore takes a fixed number of launches:
-// heights x 6 + 14 (+ one tensor launch per tuple-size class, and one per
-// node shape with a fixed kernel, tensor_fixed.cu).
+// k and levels therefore takes a bounded number of launches: heights x 6 +
+// 14, plus per round one tensor launch per tuple-size class and one per node
+// shape with a fixed kernel (tensor_fixed.cu), plus one when the key MAC has
+// both paired and single products.
 //
 // Memory: two caller buffers, the job tables (written on the first run with
 // that pair of buffers, by one host-to-device copy on the run's stream) and
@@ -661,7 +662,15 @@ int ckks_wave_workspace_size(const ckks_wave *w, size_t *table_bytes, size_t *sc
 
 int ckks_wave_describe(const ckks_wave *w, uint32_t *n_launches, uint32_t *heights) {
     if (!w || !n_launches || !heights) return CKKS_EINVAL;
-    *n_launches = (uint32_t)w->stages.size();
+    // one launch per stage, except: a fixed-shape tensor stage launches once
+    // per shape, the key MAC once for paired and once for single products
+    uint32_t n = 0;
+    for (const Stage &s : w->stages) {
+        if (s.kind == SK_TENSOR && s.fixed) n += (uint32_t)s.runs.size();
+        else if (s.kind == SK_MAC) n += (s.n_pairs > 0 ? 1u : 0u) + (s.count() > s.n_pairs ? 1u : 0u);
+        else n += 1;
+    }
+    *n_launches = n;
     *heights = (uint32_t)w->heights;
     return CKKS_OK;
 }
